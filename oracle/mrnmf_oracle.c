@@ -134,11 +134,12 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
  * (this settles the cross-processor correlation caveat of Sec. 3.2).
  *   key = (seed_lo, seed_hi), counter = (i_lo, i_hi, l / 4, 0x4D524E46)
  *   words w0..w3; pair p = (l % 4) / 2 uses (w_{2p}, w_{2p+1});
- *   u = ((w >> 8) + 0.5) * 2^-24  (exact in binary32, never 0 or 1);
+ *   u = ((w >> 9) + 0.5) * 2^-23  (an odd multiple of 2^-24: exact in
+ *   binary32 as well as binary64, never 0 or 1);
  *   Box-Muller: rho = sqrt(-2 ln u1), z = rho cos(2 pi u2) for even l,
  *   rho sin(2 pi u2) for odd l.
  */
-static double orc_u24(uint32_t w) { return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0); }
+static double orc_u23(uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 double orc_gauss_entry(uint64_t seed, int64_t row, int l)
 {
@@ -147,7 +148,7 @@ double orc_gauss_entry(uint64_t seed, int64_t row, int l)
     uint32_t w[4];
     orc_philox4x32_10(ctr, key, w);
     int p = (l & 3) >> 1;
-    double u1 = orc_u24(w[2 * p]), u2 = orc_u24(w[2 * p + 1]);
+    double u1 = orc_u23(w[2 * p]), u2 = orc_u23(w[2 * p + 1]);
     double rho = sqrt(-2.0 * log(u1));
     const double two_pi = 6.283185307179586476925286766559;
     return (l & 1) ? rho * sin(two_pi * u2) : rho * cos(two_pi * u2);
