@@ -60,7 +60,7 @@ def _load():
             lib.orc_residual.argtypes = [P, i32, i32, P, i32, P, P]
             lib.orc_spa.argtypes = [P, i32, i32, P, i32, P, P]
             lib.orc_xray.argtypes = [P, i32, i32, i32, P, P]
-            lib.orc_gp_select.argtypes = [P, i32, i32, P, i32, P, P, P, P]
+            lib.orc_gp_select.argtypes = [P, i32, i32, P, i32, P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -178,7 +178,10 @@ def xray(Y, r: int):
 
 
 def gp_select(GX, colsum_, r: int):
-    """Gaussian-projection selection (Sec. 2.3, Sec. 3.3).  Returns (K, candidates, gap)."""
+    """Gaussian-projection selection (Sec. 2.3, Sec. 3.3).
+
+    Returns (K, candidates, gap per candidate); the gap of a candidate is the
+    relative margin of the row max / min that added it."""
     GX = _f64(GX)
     k, n = GX.shape
     s = _f64(colsum_)
@@ -186,5 +189,7 @@ def gp_select(GX, colsum_, r: int):
     cand = np.zeros(2 * k, np.int32)
     nc = ctypes.c_int(0)
     gap = np.zeros(2 * k, np.float64)
-    _load().orc_gp_select(_ptr(GX), k, n, _ptr(s), r, _ptr(K), _ptr(cand), ctypes.byref(nc), _ptr(gap))
-    return K, cand[: nc.value].copy(), gap
+    cgap = np.zeros(2 * k, np.float64)
+    _load().orc_gp_select(_ptr(GX), k, n, _ptr(s), r, _ptr(K), _ptr(cand), ctypes.byref(nc), _ptr(gap),
+                          _ptr(cgap))
+    return K, cand[: nc.value].copy(), cgap[: nc.value].copy()

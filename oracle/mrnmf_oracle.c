@@ -255,7 +255,8 @@ int orc_nnls(const double* AtA, const double* Atb, double btb, int r, double* x)
             for (int q = 0; q < p; ++q) {
                 int i = idx[q];
                 if (z[i] <= 0.0) {
-                    double a = x[i] / (x[i] - z[i]);
+                    double den = x[i] - z[i];          /* >= 0; 0 only if x_i = z_i = 0 */
+                    double a = den > 0.0 ? x[i] / den : 0.0;
                     if (a < alpha) { alpha = a; blocking = i; }
                 }
             }
@@ -450,10 +451,11 @@ int orc_xray(const double* Y0, int rows, int n, int r, int32_t* K, double* gap)
  * order, append argmax_j Z(l,j) and then argmin_j Z(l,j) unless already
  * present.  cand receives up to 2k distinct indices (returned count in
  * *ncand); K = the first r of them (-1 where fewer than r exist).  gap[2l]
- * and gap[2l+1] are the relative gaps (to max_j |Z(l,j)|) of the max and min.
+ * and gap[2l+1] are the relative gaps (to max_j |Z(l,j)|) of the max and min;
+ * cand_gap[c] is the gap of the pick that added cand[c].
  */
 int orc_gp_select(const double* GX, int k, int n, const double* colsum, int r, int32_t* K,
-                  int32_t* cand, int* ncand, double* gap)
+                  int32_t* cand, int* ncand, double* gap, double* cand_gap)
 {
     int cnt = 0;
     for (int l = 0; l < k; ++l) {
@@ -476,10 +478,15 @@ int orc_gp_select(const double* GX, int k, int n, const double* colsum, int r, i
             gap[2 * l + 1] = (n > 1 && scale > 0.0) ? (s2min - zmin) / scale : 1.0;
         }
         int picks[2] = {jmax, jmin};
+        double pgap[2] = {(n > 1 && scale > 0.0) ? (zmax - s2max) / scale : 1.0,
+                          (n > 1 && scale > 0.0) ? (s2min - zmin) / scale : 1.0};
         for (int q = 0; q < 2; ++q) {
             int dup = 0;
             for (int c = 0; c < cnt; ++c) if (cand[c] == picks[q]) dup = 1;
-            if (!dup) cand[cnt++] = picks[q];
+            if (!dup) {
+                if (cand_gap) cand_gap[cnt] = pgap[q];
+                cand[cnt++] = picks[q];
+            }
         }
     }
     *ncand = cnt;
