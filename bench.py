@@ -1,0 +1,306 @@
+"""Benchmark of the single-pass TSQR reduction for near-separable NMF.
+
+One step = the whole hot path over one resident synthetic X:
+  the fused pass (R, column sums, Gaussian projection G^T X, Sec. 3.1-3.3),
+  SPA, greedy XRAY and GP selection (Sec. 2.1, 2.3), and for each selection
+  NNLS for H and the residual (Sec. 2.4).
+Metric: GB/s of X read per step (4 m n bytes / step time).
+
+Multi-GPU (torchrun): the pass has no exchange step on one box, so every rank
+runs an independent replica on its own GPU; value = bytes all ranks read /
+max over ranks of the timed wall time ("scaling": "weak").
+
+--impl reference times the FP64 CPU oracle (the only reference this project
+has) on the host cores on a bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TSQR pass GB/s of X (% of HBM roofline), mixed vs FP32, at stated R error"
+WORKLOAD = "near_sep_1e7x50"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def _fp32_simt_peak_tflops(sms: int, mhz: float) -> float:
+    # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_step(X: np.ndarray, w, rows: int):
+    """The oracle's whole path on the first `rows` rows of X; returns seconds."""
+    import oracle
+    oracle.build()
+    Xs = X[:rows].astype(np.float64)
+    t0 = time.perf_counter()
+    R = oracle.qr_r(Xs)
+    s = oracle.colsum(Xs)
+    GX = oracle.gauss_project(Xs, w.k, w.seed)
+    for K in (oracle.spa(R, s, w.r)[0], oracle.xray(R, w.r)[0], oracle.gp_select(GX, s, w.r)[0]):
+        if np.all(K >= 0):
+            H, _ = oracle.nnls_h(R, K)
+            oracle.residual(R, K, H)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    from paper_1402_6964_gb300 import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = synth.WORKLOADS[args.workload]
+    rows = args.ref_rows
+    X, _ = synth.workload_matrix(w, m=rows)
+    for _ in range(args.warmup):
+        cpu_oracle_step(X, w, rows)
+    ts = [cpu_oracle_step(X, w, rows) for _ in range(args.steps)]
+    t = sum(ts)
+    gbs = 4.0 * rows * w.n * args.steps / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "m": w.m, "n": w.n, "r": w.r, "k": w.k, "parallelism": "replicas"},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {rows} rows of the {w.m}-row workload per step"},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1402_6964_gb300 import build, mrnmf, synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    w = synth.WORKLOADS[args.workload]
+    X, P = synth.workload_matrix(w)
+    m, n, r, k = X.shape[0], w.n, w.r, w.k
+    Xd = torch.from_numpy(X).cuda()
+    dev = Xd.device
+    h = mrnmf.Handle()
+    stream = torch.cuda.current_stream()
+    R = torch.empty((n, n), dtype=torch.float64, device=dev)
+    cs = torch.empty(n, dtype=torch.float64, device=dev)
+    GX = torch.empty((k, n), dtype=torch.float64, device=dev)
+    Ks = {mth: (torch.empty(r, dtype=torch.int32, device=dev), torch.empty(r, dtype=torch.float64, device=dev))
+          for mth in ("spa", "xray", "gp")}
+    Hs = {mth: torch.empty((r, n), dtype=torch.float64, device=dev) for mth in Ks}
+    outs = {mth: torch.empty(2, dtype=torch.float64, device=dev) for mth in Ks}
+
+    def step():
+        h.tsqr_gp(Xd, k, w.seed, prec=args.prec, out=(R, cs, GX))
+        for mth in ("spa", "xray", "gp"):
+            h.select_extreme(mth, R=R, colsum=cs, GX=GX if mth == "gp" else None, r=r, out=Ks[mth])
+            h.nnls_h(R, Ks[mth][0], out=Hs[mth])
+            h.residual(R, Ks[mth][0], Hs[mth], out=outs[mth])
+
+    for _ in range(args.warmup):
+        step()
+    h.sync()
+
+    leaf_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = mrnmf.kernel_launches()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    step_ev[0].record(stream)
+    for i in range(args.steps):
+        h.profile_events(*leaf_ev[i])
+        step()
+        step_ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = mrnmf.kernel_launches() - launches0
+    h.profile_events(None, None)
+    h.sync()
+    t_dev = step_ev[0].elapsed_time(step_ev[-1]) / 1e3  # seconds
+    leaf_ms = [a.elapsed_time(b) for a, b in leaf_ev]
+    t_max = t_dev
+    if world > 1:
+        tt = torch.tensor([t_dev], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+
+    bytes_step = 4.0 * m * n
+    value = bytes_step * args.steps * world / t_max / 1e9
+    hbm, mhz, peak_src = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    leaf_s = statistics.mean(leaf_ms) / 1e3
+    leaf_gbs = bytes_step / leaf_s / 1e9
+    flops = 2.0 * m * n * n
+    simt_peak = _fp32_simt_peak_tflops(sms, mhz)
+    leaf_tflops = flops / leaf_s / 1e12
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "leaf_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            td = json.load(open(tfile))
+            if td.get("kernel_hash") == build._stamp():
+                traffic = td.get("traffic_bytes_per_launch")
+        except Exception:
+            traffic = None
+    roof_hbm = {"bound": "hbm", "achieved": leaf_gbs, "peak": hbm, "unit": "GB/s", "frac": leaf_gbs / hbm,
+                "traffic": traffic, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    roof_alu = {"bound": "alu", "achieved": leaf_tflops, "peak": simt_peak, "unit": "TFLOP/s",
+                "frac": leaf_tflops / simt_peak, "traffic": traffic,
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"}
+    roofline = roof_hbm if roof_hbm["frac"] >= roof_alu["frac"] else roof_alu
+
+    # R error of this pass vs the unique R (Cholesky of the FP64 Gram, host)
+    Rg = R.cpu().numpy()
+    G = X.astype(np.float64)
+    Gram = G.T @ G
+    del G
+    Rc = np.linalg.cholesky(Gram).T
+    r_err = float(np.linalg.norm(Rg - Rc) / np.linalg.norm(Rc))
+    K_spa = sorted(Ks["spa"][0].cpu().numpy().tolist())
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        Xp = torch.from_numpy(X).pin_memory()
+        h.factorize_host(Xp, r, method="spa", k=0, seed=w.seed, prec=args.prec)  # warm-up
+        ne = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            h.factorize_host(Xp, r, method="spa", k=0, seed=w.seed, prec=args.prec)
+        te = (time.perf_counter() - t0) / ne
+        e2e = {"value": bytes_step / te / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(bytes_step),
+               "d2h_bytes_per_step": int(4 * r + 8 * r * n + 16), "ms_per_step": te * 1e3,
+               "call": "mrnmf_factorize_host (SPA, H, residual)"}
+        del Xp
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rows = args.cpu_rows
+        tcpu = cpu_oracle_step(X, w, rows)
+        cpu = {"value": 4.0 * rows * n / tcpu / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {rows} rows of the workload (pass + SPA/XRAY/GP + NNLS + residual), "
+                         f"{tcpu:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name, "m": m, "n": n, "r": r, "k": k, "prec": args.prec,
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "l2": "input (2.0 GB) larger than L2 (129 MB); no flush needed"},
+                "roofline": roofline, "roofline_other": roof_alu if roofline is roof_hbm else roof_hbm,
+                "leaf_ms": statistics.mean(leaf_ms), "r_error": {"rel_fro_vs_chol_gram": r_err},
+                "K_spa": K_spa, "K_planted": P.K.tolist(),
+                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "cpu_baseline": cpu,
+                "wall_s_timed": t_wall}
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["auto", "fp32", "tf32x3"], default="auto")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=1_000_000)
+    ap.add_argument("--ref-rows", type=int, default=250_000)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * mrnmf.h -- C ABI of the GB300 single-pass reduction for near-separable NMF
+ * of tall-and-skinny matrices (Benson, Lee, Rajwa, Gleich, arXiv 1402.6964).
+ *
+ * The method (Sec. 1.1, Sec. 2): a nonnegative m-by-n X (m >> n) is
+ * near-separable, X ~ X(:,K) H with |K| = r.  One pass over X produces the
+ * n-by-n triangular factor R of its thin QR (Sec. 3.1), the column sums of X
+ * (Sec. 3.3) and, optionally, the Gaussian projection G^T X (Sec. 2.3,
+ * Algorithm 1).  Because X = X(:,K)H implies R = R(:,K)H (Sec. 2.2), the
+ * extreme columns K, the coefficients H and the residual are then computed
+ * from R at n-by-n size (Sec. 2.1, Sec. 2.4).
+ *
+ * General rules for every entry point:
+ *  - Pointers named "device" are CUDA device (or managed) memory owned by the
+ *    caller; the library never frees or keeps them past the call's work.
+ *  - Matrices are dense row-major: X[i*ldx + j], R[i*n + j] (upper
+ *    triangular, diag >= 0, zeros below), H[t*n + j] (r-by-n), GX[l*n + j]
+ *    (k-by-n).  K holds 0-based column indices.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it and the call returns without waiting.  Argument errors
+ *    are returned at once and enqueue nothing.  Errors found on the device
+ *    (negative / NaN / zero-sum input, NNLS not converged, a bounded wait
+ *    that timed out) are recorded in a device status word of the handle and
+ *    returned by mrnmf_sync_status().
+ *  - A handle owns its device workspace and is not thread-safe: use one
+ *    handle per host thread, or serialise calls on it.  Calls on one handle
+ *    that overlap on the GPU (different streams) race on its workspace.
+ *  - No entry point falls back to the CPU.
+ *  - Limits: 1 <= n <= MRNMF_NMAX, m >= n, 1 <= r <= n, 1 <= k <= MRNMF_KMAX.
+ */
+#ifndef MRNMF_H
+#define MRNMF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MRNMF_NMAX 256
+#define MRNMF_KMAX 64
+
+typedef enum {
+    MRNMF_OK = 0,
+    MRNMF_ERR_INVALID_ARG = 1,
+    MRNMF_ERR_CUDA = 2,
+    MRNMF_ERR_NO_MEMORY = 3,
+    MRNMF_ERR_NOT_CONVERGED = 4,
+    MRNMF_ERR_TIMEOUT = 5,
+    MRNMF_ERR_BAD_INPUT = 6,       /* negative or NaN entry, or a zero column sum */
+    MRNMF_ERR_RANK_DEFICIENT = 7   /* R(:,K) singular, or fewer than r GP candidates */
+} mrnmf_status;
+
+typedef enum { MRNMF_F32 = 0, MRNMF_F64 = 1 } mrnmf_dtype;
+
+/* Arithmetic of the pass.  FP64: everything in binary64 (X must be F64).
+ * FP32: binary32 SIMT Householder.  TF32X3: binary32 reflectors with the
+ * blocked trailing update on tcgen05 tensor cores in 3-pass split TF32
+ * (hi*hi + hi*lo + lo*hi), FP32 accumulation.  AUTO picks FP64 for F64
+ * input, otherwise the fastest form available for n. */
+typedef enum { MRNMF_PREC_AUTO = 0, MRNMF_PREC_FP64 = 1, MRNMF_PREC_FP32 = 2, MRNMF_PREC_TF32X3 = 3 } mrnmf_prec;
+
+typedef enum { MRNMF_SPA = 0, MRNMF_XRAY = 1, MRNMF_GP = 2 } mrnmf_method;
+
+typedef struct mrnmf_handle mrnmf_handle;
+
+/* Create / destroy a handle.  mrnmf_create selects no device: the handle
+ * works on the device that is current when each call is made. */
+mrnmf_status mrnmf_create(mrnmf_handle** handle);
+void mrnmf_destroy(mrnmf_handle* handle);
+
+/* Human-readable text of the last error on this handle (never NULL). */
+const char* mrnmf_last_error_string(const mrnmf_handle* handle);
+
+/* Wait for `stream`, then return (and clear) the first error any kernel of
+ * this handle recorded on the device since the last call. */
+mrnmf_status mrnmf_sync_status(mrnmf_handle* handle, void* stream);
+
+/*
+ * R factor of the thin QR of X (Sec. 3.1: TSQR; only R is formed, Q stays
+ * implicit) and the column sums of X (Sec. 3.3), in one read of X.
+ *   X      device, m-by-n row-major, leading dimension ldx >= n, dtype F32/F64
+ *   R      device, n*n doubles out: upper triangular, diag >= 0
+ *   colsum device, n doubles out (nullable)
+ * With a full-column-rank X, R is unique and matches the FP64 oracle to the
+ * form's stated error.  X must be nonnegative (the method's NMF setting):
+ * a negative or NaN entry sets MRNMF_ERR_BAD_INPUT on the device.
+ */
+mrnmf_status mrnmf_tsqr_r(mrnmf_handle* handle, const void* X, int64_t m, int32_t n, int64_t ldx,
+                          int32_t dtype, int32_t prec, double* R, double* colsum, void* stream);
+
+/*
+ * Gaussian projection GX = G^T X (Sec. 2.3; Algorithm 1 with its combiner,
+ * Sec. 3.2) and the column sums of X, in one read of X.  G is m-by-k with
+ * i.i.d. N(0,1) entries drawn by Philox4x32-10 keyed by `seed` and the global
+ * row index (row_offset + i), so G does not depend on how rows are split:
+ *   key = (seed_lo, seed_hi), counter = (row_lo, row_hi, l/4, 0x4D524E46),
+ *   u = ((w >> 9) + 0.5) 2^-23, Box-Muller pairs (w0,w1) -> l%4 = 0,1 and
+ *   (w2,w3) -> l%4 = 2,3, cosine for even l and sine for odd l.
+ *   GX     device, k*n doubles out
+ *   colsum device, n doubles out (nullable)
+ */
+mrnmf_status mrnmf_gauss_project(mrnmf_handle* handle, const void* X, int64_t m, int32_t n, int64_t ldx,
+                                 int32_t dtype, int32_t k, uint64_t seed, int64_t row_offset,
+                                 double* GX, double* colsum, void* stream);
+
+/*
+ * The one-pass form of Sec. 3.5: R, the column sums and (if k > 0) GX from a
+ * single read of X.  Arguments as in mrnmf_tsqr_r and mrnmf_gauss_project;
+ * GX may be NULL when k == 0.
+ */
+mrnmf_status mrnmf_tsqr_gp(mrnmf_handle* handle, const void* X, int64_t m, int32_t n, int64_t ldx,
+                           int32_t dtype, int32_t prec, double* R, double* colsum,
+                           int32_t k, uint64_t seed, double* GX, void* stream);
+
+/*
+ * Extreme-column selection at n-by-n size (Sec. 2.1, Sec. 2.3).
+ *   MRNMF_SPA : SPA on R D^-1 (D = diag(colsum)): repeatedly pick the column
+ *               of largest 2-norm and project it out of all columns.
+ *   MRNMF_XRAY: greedy XRAY on R: pick argmax_j ||Res^T R(:,j)|| / ||R(:,j)||,
+ *               Res = R - R(:,K) H with H refreshed by NNLS after each pick.
+ *   MRNMF_GP  : for each row l of GX D^-1 in order, append argmax then argmin,
+ *               skipping duplicates; K = first r distinct.
+ * Ties go to the lowest index.
+ *   R      device n*n doubles (SPA, XRAY)      colsum device n doubles (SPA, GP)
+ *   GX     device k*n doubles (GP only; NULL otherwise)
+ *   K      device r int32 out                   gap device r doubles out (nullable):
+ *          relative gap between the best and second-best score of each pick
+ *          (GP: of the row's max), -1 where the best score is zero to rounding.
+ */
+mrnmf_status mrnmf_select_extreme(mrnmf_handle* handle, int32_t method, const double* R, int32_t n,
+                                  const double* colsum, const double* GX, int32_t k, int32_t r,
+                                  int32_t* K, double* gap, void* stream);
+
+/*
+ * H(:,i) = argmin_{y >= 0} || R(:,K) y - R(:,i) ||_2 for i = 0..n-1 (Sec. 2.4),
+ * by Lawson-Hanson active sets on the FP64 normal equations.
+ *   R device n*n, K device r int32, H device r*n doubles out.
+ * MRNMF_ERR_NOT_CONVERGED / MRNMF_ERR_RANK_DEFICIENT surface at sync.
+ */
+mrnmf_status mrnmf_nnls_h(mrnmf_handle* handle, const double* R, int32_t n, const int32_t* K, int32_t r,
+                          double* H, void* stream);
+
+/*
+ * out[0] = ||R - R(:,K) H||_F (= ||X - X(:,K)H||_F, Sec. 2.4),
+ * out[1] = ||R - R(:,K) H||_F^2 / ||R||_F^2 (the relative error of Sec. 4).
+ *   out device, 2 doubles.
+ */
+mrnmf_status mrnmf_residual(mrnmf_handle* handle, const double* R, int32_t n, const int32_t* K, int32_t r,
+                            const double* H, double* out, void* stream);
+
+/*
+ * Streaming form of the pass (Sec. 3.4: one pass over data that arrives in
+ * pieces).  begin() resets the handle's running state for n columns;
+ * push() folds `rows` more rows into it (X_chunk device, row-major, ldx);
+ * end() reduces the state to R / colsum / GX exactly as mrnmf_tsqr_gp would
+ * for the concatenated rows.  Gaussian rows are keyed by the global row
+ * index, so the result does not depend on how the rows were split.
+ * Only one stream may be open per handle.
+ */
+mrnmf_status mrnmf_stream_begin(mrnmf_handle* handle, int32_t n, int32_t dtype, int32_t prec,
+                                int32_t k, uint64_t seed, void* stream);
+mrnmf_status mrnmf_stream_push(mrnmf_handle* handle, const void* X_chunk, int64_t rows, int64_t ldx,
+                               void* stream);
+mrnmf_status mrnmf_stream_end(mrnmf_handle* handle, double* R, double* colsum, double* GX, void* stream);
+
+/*
+ * End-to-end factorisation from HOST memory: streams X (host, row-major
+ * float32, m-by-n, ldx) to the device in chunks with the copies overlapped
+ * with the pass, then selects K by `method`, solves H and the residual, and
+ * copies K (r int32), H (r*n doubles), resid (2 doubles) and, if non-NULL,
+ * R (n*n doubles) back to host memory.  Synchronous: returns when the host
+ * outputs are written (device-side errors are returned directly).
+ * Pinned (page-locked) X gives the full copy bandwidth.
+ */
+mrnmf_status mrnmf_factorize_host(mrnmf_handle* handle, const float* X, int64_t m, int32_t n, int64_t ldx,
+                                  int32_t prec, int32_t method, int32_t r, int32_t k, uint64_t seed,
+                                  int32_t* K, double* H, double* resid, double* R, void* stream);
+
+/*
+ * Instrumentation (no counterpart in the paper; used by benchmarks).
+ * mrnmf_profile_events: when both are non-NULL, every later pass on this
+ * handle records `ev_start` / `ev_stop` (cudaEvent_t created by the caller)
+ * on its stream immediately before and after the leaf kernel -- the kernel
+ * that reads X -- so its duration can be read with cudaEventElapsedTime.
+ * Pass NULLs to stop.  mrnmf_kernel_launches: number of CUDA kernels this
+ * library has launched in the calling process so far.
+ */
+mrnmf_status mrnmf_profile_events(mrnmf_handle* handle, void* ev_start, void* ev_stop);
+uint64_t mrnmf_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRNMF_H */

@@ -1,0 +1,447 @@
+// api.cu -- the extern "C" entry points of include/mrnmf.h.
+//
+// Argument checking, the handle's device workspace, stream ordering, and the
+// composition of the pass kernels (tsqr_simt.cu / tsqr_tc.cu) and the n-by-n
+// step kernels (small_step.cu).  No entry point computes on the host.
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/mrnmf.h"
+#include "internal.h"
+
+struct mrnmf_handle {
+    int device = -1;
+    int* d_status = nullptr;
+    void* ws = nullptr;  // pass state
+    size_t ws_bytes = 0;
+    void* sws = nullptr;  // small-step workspace
+    size_t sws_bytes = 0;
+    std::string err = "no error";
+    // streaming
+    bool open = false;
+    int xdtype = MRNMF_F32;
+    mrnmf::PassState st;
+    // host end-to-end path
+    void* xbuf = nullptr;
+    size_t xbuf_bytes = 0;
+    double* dout = nullptr;
+    size_t dout_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+    cudaEvent_t ev_done[2] = {nullptr, nullptr};
+    // instrumentation
+    cudaEvent_t prof_start = nullptr, prof_stop = nullptr;
+};
+
+namespace {
+
+mrnmf_status fail(mrnmf_handle* h, mrnmf_status s, const std::string& msg)
+{
+    if (h) h->err = msg;
+    return s;
+}
+
+mrnmf_status cuda_fail(mrnmf_handle* h, cudaError_t e, const char* where)
+{
+    return fail(h, e == cudaErrorMemoryAllocation ? MRNMF_ERR_NO_MEMORY : MRNMF_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+mrnmf_status bind_device(mrnmf_handle* h)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetDevice");
+    if (h->device < 0) {
+        h->device = dev;
+        e = cudaMalloc(&h->d_status, 256);
+        if (e != cudaSuccess) return cuda_fail(h, e, "status word");
+        e = cudaMemset(h->d_status, 0, 256);
+        if (e != cudaSuccess) return cuda_fail(h, e, "status word");
+    } else if (h->device != dev) {
+        return fail(h, MRNMF_ERR_INVALID_ARG, "handle is bound to device " + std::to_string(h->device) +
+                                                  " but device " + std::to_string(dev) + " is current");
+    }
+    return MRNMF_OK;
+}
+
+mrnmf_status grow(mrnmf_handle* h, void** buf, size_t* have, size_t need, const char* what)
+{
+    if (need <= *have) return MRNMF_OK;
+    if (*buf) {
+        cudaError_t e = cudaFree(*buf);  // synchronises with work that may still use it
+        *buf = nullptr;
+        *have = 0;
+        if (e != cudaSuccess) return cuda_fail(h, e, what);
+    }
+    cudaError_t e = cudaMalloc(buf, need);
+    if (e != cudaSuccess) return cuda_fail(h, e, what);
+    *have = need;
+    return MRNMF_OK;
+}
+
+int resolve_prec(int prec, int dtype, int n)
+{
+    if (prec == MRNMF_PREC_AUTO) {
+        if (dtype == MRNMF_F64) return MRNMF_PREC_FP64;
+        return mrnmf::tc_supported(n) ? MRNMF_PREC_TF32X3 : MRNMF_PREC_FP32;
+    }
+    return prec;
+}
+
+mrnmf_status check_pass_args(mrnmf_handle* h, const void* X, int64_t m, int32_t n, int64_t ldx, int32_t dtype,
+                             int32_t prec, int32_t k)
+{
+    if (!h) return MRNMF_ERR_INVALID_ARG;
+    if (!X) return fail(h, MRNMF_ERR_INVALID_ARG, "X is NULL");
+    if (n < 1 || n > MRNMF_NMAX) return fail(h, MRNMF_ERR_INVALID_ARG, "n must be in [1, 256]");
+    if (m < n) return fail(h, MRNMF_ERR_INVALID_ARG, "need m >= n (tall-and-skinny X)");
+    if (ldx < n) return fail(h, MRNMF_ERR_INVALID_ARG, "ldx < n");
+    if (dtype != MRNMF_F32 && dtype != MRNMF_F64) return fail(h, MRNMF_ERR_INVALID_ARG, "dtype must be F32 or F64");
+    if (prec < MRNMF_PREC_AUTO || prec > MRNMF_PREC_TF32X3) return fail(h, MRNMF_ERR_INVALID_ARG, "bad prec");
+    if (k < 0 || k > MRNMF_KMAX) return fail(h, MRNMF_ERR_INVALID_ARG, "k must be in [0, 64]");
+    return MRNMF_OK;
+}
+
+// Set up h->st for a pass: precision, stream count, workspace.
+mrnmf_status setup_pass(mrnmf_handle* h, int n, int dtype, int prec, int k, uint64_t seed, int64_t m_hint)
+{
+    prec = resolve_prec(prec, dtype, n);
+    if (prec == MRNMF_PREC_FP32 && dtype == MRNMF_F64)
+        return fail(h, MRNMF_ERR_INVALID_ARG, "FP32 pass needs F32 input (the library never narrows X)");
+    if (prec == MRNMF_PREC_TF32X3 && (dtype != MRNMF_F32 || !mrnmf::tc_supported(n)))
+        return fail(h, MRNMF_ERR_INVALID_ARG, "TF32X3 pass needs F32 input and a supported n");
+    mrnmf::PassState st;
+    st.n = n;
+    st.k = k;
+    st.fp64 = prec == MRNMF_PREC_FP64;
+    st.tc = prec == MRNMF_PREC_TF32X3;
+    st.seed = seed;
+    st.rows_seen = 0;
+    st.P = mrnmf::choose_streams(n, k, st.fp64, st.tc, m_hint);
+    mrnmf_status s = grow(h, &h->ws, &h->ws_bytes, mrnmf::pass_state_bytes(n, k, st.P, st.fp64), "pass workspace");
+    if (s != MRNMF_OK) return s;
+    mrnmf::pass_state_carve(st, h->ws);
+    st.ev_leaf_start = h->prof_start;
+    st.ev_leaf_stop = h->prof_stop;
+    h->st = st;
+    return MRNMF_OK;
+}
+
+mrnmf_status run_pass(mrnmf_handle* h, const void* X, int64_t m, int32_t n, int64_t ldx, int32_t dtype, int32_t prec,
+                      int qr, double* R, double* colsum, int32_t k, uint64_t seed, int64_t row_offset, double* GX,
+                      cudaStream_t s)
+{
+    mrnmf_status st = setup_pass(h, n, dtype, prec, k, seed, m);
+    if (st != MRNMF_OK) return st;
+    h->st.rows_seen = row_offset;
+    cudaError_t e = mrnmf::pass_reset(h->st, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pass reset");
+    e = mrnmf::pass_push(h->st, X, m, ldx, dtype == MRNMF_F64, qr, h->d_status, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pass");
+    e = mrnmf::pass_finish(h->st, qr, R, colsum, GX, h->d_status, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "tree / finalize");
+    return MRNMF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mrnmf_status mrnmf_create(mrnmf_handle** handle)
+{
+    if (!handle) return MRNMF_ERR_INVALID_ARG;
+    *handle = new (std::nothrow) mrnmf_handle();
+    return *handle ? MRNMF_OK : MRNMF_ERR_NO_MEMORY;
+}
+
+void mrnmf_destroy(mrnmf_handle* h)
+{
+    if (!h) return;
+    if (h->device >= 0) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(h->device);
+        cudaDeviceSynchronize();
+        cudaFree(h->d_status);
+        cudaFree(h->ws);
+        cudaFree(h->sws);
+        cudaFree(h->xbuf);
+        cudaFree(h->dout);
+        for (int i = 0; i < 2; ++i) {
+            if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
+            if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
+        }
+        if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+        cudaSetDevice(cur);
+    }
+    delete h;
+}
+
+const char* mrnmf_last_error_string(const mrnmf_handle* h)
+{
+    return h ? h->err.c_str() : "NULL handle";
+}
+
+mrnmf_status mrnmf_sync_status(mrnmf_handle* h, void* stream)
+{
+    if (!h) return MRNMF_ERR_INVALID_ARG;
+    if (h->device < 0) return MRNMF_OK;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream");
+    int code = 0;
+    e = cudaMemcpy(&code, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+    if (code != 0) {
+        e = cudaMemset(h->d_status, 0, sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
+        const char* what = code == MRNMF_ERR_BAD_INPUT        ? "input has a negative or NaN entry, or a zero column"
+                           : code == MRNMF_ERR_NOT_CONVERGED  ? "NNLS did not converge"
+                           : code == MRNMF_ERR_RANK_DEFICIENT ? "R(:,K) is singular or too few GP candidates"
+                           : code == MRNMF_ERR_TIMEOUT        ? "a bounded device wait timed out"
+                                                              : "device error";
+        return fail(h, (mrnmf_status)code, what);
+    }
+    return MRNMF_OK;
+}
+
+mrnmf_status mrnmf_tsqr_r(mrnmf_handle* h, const void* X, int64_t m, int32_t n, int64_t ldx, int32_t dtype,
+                          int32_t prec, double* R, double* colsum, void* stream)
+{
+    mrnmf_status s = check_pass_args(h, X, m, n, ldx, dtype, prec, 0);
+    if (s != MRNMF_OK) return s;
+    if (!R) return fail(h, MRNMF_ERR_INVALID_ARG, "R is NULL");
+    if ((s = bind_device(h)) != MRNMF_OK) return s;
+    return run_pass(h, X, m, n, ldx, dtype, prec, 1, R, colsum, 0, 0, 0, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+mrnmf_status mrnmf_gauss_project(mrnmf_handle* h, const void* X, int64_t m, int32_t n, int64_t ldx, int32_t dtype,
+                                 int32_t k, uint64_t seed, int64_t row_offset, double* GX, double* colsum,
+                                 void* stream)
+{
+    mrnmf_status s = check_pass_args(h, X, m, n, ldx, dtype, MRNMF_PREC_AUTO, k);
+    if (s != MRNMF_OK) return s;
+    if (k < 1 || !GX) return fail(h, MRNMF_ERR_INVALID_ARG, "need k >= 1 and GX");
+    if (row_offset < 0) return fail(h, MRNMF_ERR_INVALID_ARG, "row_offset < 0");
+    if ((s = bind_device(h)) != MRNMF_OK) return s;
+    const int prec = dtype == MRNMF_F64 ? MRNMF_PREC_FP64 : MRNMF_PREC_FP32;
+    return run_pass(h, X, m, n, ldx, dtype, prec, 0, nullptr, colsum, k, seed, row_offset, GX,
+                    static_cast<cudaStream_t>(stream));
+}
+
+mrnmf_status mrnmf_tsqr_gp(mrnmf_handle* h, const void* X, int64_t m, int32_t n, int64_t ldx, int32_t dtype,
+                           int32_t prec, double* R, double* colsum, int32_t k, uint64_t seed, double* GX,
+                           void* stream)
+{
+    mrnmf_status s = check_pass_args(h, X, m, n, ldx, dtype, prec, k);
+    if (s != MRNMF_OK) return s;
+    if (!R) return fail(h, MRNMF_ERR_INVALID_ARG, "R is NULL");
+    if (k > 0 && !GX) return fail(h, MRNMF_ERR_INVALID_ARG, "k > 0 needs GX");
+    if ((s = bind_device(h)) != MRNMF_OK) return s;
+    return run_pass(h, X, m, n, ldx, dtype, prec, 1, R, colsum, k, seed, 0, k > 0 ? GX : nullptr,
+                    static_cast<cudaStream_t>(stream));
+}
+
+mrnmf_status mrnmf_select_extreme(mrnmf_handle* h, int32_t method, const double* R, int32_t n, const double* colsum,
+                                  const double* GX, int32_t k, int32_t r, int32_t* K, double* gap, void* stream)
+{
+    if (!h) return MRNMF_ERR_INVALID_ARG;
+    if (n < 1 || n > MRNMF_NMAX) return fail(h, MRNMF_ERR_INVALID_ARG, "n must be in [1, 256]");
+    if (r < 1 || r > n) return fail(h, MRNMF_ERR_INVALID_ARG, "need 1 <= r <= n");
+    if (!K) return fail(h, MRNMF_ERR_INVALID_ARG, "K is NULL");
+    if (method == MRNMF_SPA) {
+        if (!R || !colsum) return fail(h, MRNMF_ERR_INVALID_ARG, "SPA needs R and colsum");
+    } else if (method == MRNMF_XRAY) {
+        if (!R) return fail(h, MRNMF_ERR_INVALID_ARG, "XRAY needs R");
+        if (r > 64) return fail(h, MRNMF_ERR_INVALID_ARG, "XRAY supports r <= 64");
+    } else if (method == MRNMF_GP) {
+        if (!GX || !colsum || k < 1 || k > MRNMF_KMAX)
+            return fail(h, MRNMF_ERR_INVALID_ARG, "GP needs GX, colsum and 1 <= k <= 64");
+    } else {
+        return fail(h, MRNMF_ERR_INVALID_ARG, "unknown method");
+    }
+    mrnmf_status s = bind_device(h);
+    if (s != MRNMF_OK) return s;
+    if ((s = grow(h, &h->sws, &h->sws_bytes, mrnmf::small_ws_bytes(n, k, r), "small-step workspace")) != MRNMF_OK)
+        return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (method == MRNMF_SPA) e = mrnmf::select_spa(R, n, colsum, r, K, gap, h->sws, h->d_status, st);
+    else if (method == MRNMF_XRAY) e = mrnmf::select_xray(R, n, r, K, gap, h->sws, h->d_status, st);
+    else e = mrnmf::select_gp(GX, k, n, colsum, r, K, gap, h->sws, h->d_status, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "select");
+    return MRNMF_OK;
+}
+
+mrnmf_status mrnmf_nnls_h(mrnmf_handle* h, const double* R, int32_t n, const int32_t* K, int32_t r, double* H,
+                          void* stream)
+{
+    if (!h) return MRNMF_ERR_INVALID_ARG;
+    if (!R || !K || !H) return fail(h, MRNMF_ERR_INVALID_ARG, "NULL argument");
+    if (n < 1 || n > MRNMF_NMAX || r < 1 || r > n || r > 64)
+        return fail(h, MRNMF_ERR_INVALID_ARG, "need 1 <= r <= min(n, 64), n <= 256");
+    mrnmf_status s = bind_device(h);
+    if (s != MRNMF_OK) return s;
+    if ((s = grow(h, &h->sws, &h->sws_bytes, mrnmf::small_ws_bytes(n, 0, r), "small-step workspace")) != MRNMF_OK)
+        return s;
+    cudaError_t e = mrnmf::nnls_h(R, n, K, r, H, h->sws, h->d_status, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(h, e, "nnls");
+    return MRNMF_OK;
+}
+
+mrnmf_status mrnmf_residual(mrnmf_handle* h, const double* R, int32_t n, const int32_t* K, int32_t r, const double* H,
+                            double* out, void* stream)
+{
+    if (!h) return MRNMF_ERR_INVALID_ARG;
+    if (!R || !K || !H || !out) return fail(h, MRNMF_ERR_INVALID_ARG, "NULL argument");
+    if (n < 1 || n > MRNMF_NMAX || r < 1 || r > n) return fail(h, MRNMF_ERR_INVALID_ARG, "need 1 <= r <= n <= 256");
+    mrnmf_status s = bind_device(h);
+    if (s != MRNMF_OK) return s;
+    if ((s = grow(h, &h->sws, &h->sws_bytes, mrnmf::small_ws_bytes(n, 0, r), "small-step workspace")) != MRNMF_OK)
+        return s;
+    cudaError_t e = mrnmf::residual(R, n, K, r, H, out, h->sws, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(h, e, "residual");
+    return MRNMF_OK;
+}
+
+mrnmf_status mrnmf_stream_begin(mrnmf_handle* h, int32_t n, int32_t dtype, int32_t prec, int32_t k, uint64_t seed,
+                                void* stream)
+{
+    if (!h) return MRNMF_ERR_INVALID_ARG;
+    if (n < 1 || n > MRNMF_NMAX) return fail(h, MRNMF_ERR_INVALID_ARG, "n must be in [1, 256]");
+    if (dtype != MRNMF_F32 && dtype != MRNMF_F64) return fail(h, MRNMF_ERR_INVALID_ARG, "bad dtype");
+    if (prec < MRNMF_PREC_AUTO || prec > MRNMF_PREC_TF32X3) return fail(h, MRNMF_ERR_INVALID_ARG, "bad prec");
+    if (k < 0 || k > MRNMF_KMAX) return fail(h, MRNMF_ERR_INVALID_ARG, "k must be in [0, 64]");
+    mrnmf_status s = bind_device(h);
+    if (s != MRNMF_OK) return s;
+    if ((s = setup_pass(h, n, dtype, prec, k, seed, 0)) != MRNMF_OK) return s;
+    h->xdtype = dtype;
+    cudaError_t e = mrnmf::pass_reset(h->st, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream begin");
+    h->open = true;
+    return MRNMF_OK;
+}
+
+mrnmf_status mrnmf_stream_push(mrnmf_handle* h, const void* X_chunk, int64_t rows, int64_t ldx, void* stream)
+{
+    if (!h) return MRNMF_ERR_INVALID_ARG;
+    if (!h->open) return fail(h, MRNMF_ERR_INVALID_ARG, "no open stream (call mrnmf_stream_begin)");
+    if (rows < 0 || (rows > 0 && !X_chunk) || ldx < h->st.n) return fail(h, MRNMF_ERR_INVALID_ARG, "bad chunk");
+    mrnmf_status s = bind_device(h);
+    if (s != MRNMF_OK) return s;
+    cudaError_t e = mrnmf::pass_push(h->st, X_chunk, rows, ldx, h->xdtype == MRNMF_F64, 1, h->d_status,
+                                     static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream push");
+    return MRNMF_OK;
+}
+
+mrnmf_status mrnmf_stream_end(mrnmf_handle* h, double* R, double* colsum, double* GX, void* stream)
+{
+    if (!h) return MRNMF_ERR_INVALID_ARG;
+    if (!h->open) return fail(h, MRNMF_ERR_INVALID_ARG, "no open stream");
+    if (!R) return fail(h, MRNMF_ERR_INVALID_ARG, "R is NULL");
+    if (h->st.rows_seen < h->st.n) return fail(h, MRNMF_ERR_INVALID_ARG, "fewer rows than columns were pushed");
+    mrnmf_status s = bind_device(h);
+    if (s != MRNMF_OK) return s;
+    h->open = false;
+    cudaError_t e = mrnmf::pass_finish(h->st, 1, R, colsum, h->st.k > 0 ? GX : nullptr, h->d_status,
+                                       static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream end");
+    return MRNMF_OK;
+}
+
+mrnmf_status mrnmf_factorize_host(mrnmf_handle* h, const float* X, int64_t m, int32_t n, int64_t ldx, int32_t prec,
+                                  int32_t method, int32_t r, int32_t k, uint64_t seed, int32_t* K, double* H,
+                                  double* resid, double* R, void* stream)
+{
+    mrnmf_status s = check_pass_args(h, X, m, n, ldx, MRNMF_F32, prec, method == MRNMF_GP ? k : 0);
+    if (s != MRNMF_OK) return s;
+    if (!K || !H || !resid) return fail(h, MRNMF_ERR_INVALID_ARG, "K, H and resid are required");
+    if (r < 1 || r > n || r > 64) return fail(h, MRNMF_ERR_INVALID_ARG, "need 1 <= r <= min(n, 64)");
+    if (method < MRNMF_SPA || method > MRNMF_GP) return fail(h, MRNMF_ERR_INVALID_ARG, "unknown method");
+    if (method == MRNMF_GP && k < 1) return fail(h, MRNMF_ERR_INVALID_ARG, "GP needs k >= 1");
+    if ((s = bind_device(h)) != MRNMF_OK) return s;
+    const int kk = method == MRNMF_GP ? k : 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (!h->copy_stream) {
+        if ((e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(h, e, "copy stream");
+        for (int i = 0; i < 2; ++i) {
+            if ((e = cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(h, e, "events");
+        }
+    }
+    // two staging buffers of up to 64 MiB each
+    const int64_t row_bytes = (int64_t)n * 4;
+    int64_t chunk = std::max<int64_t>(1, (64ll << 20) / row_bytes);
+    if (chunk > m) chunk = m;
+    if ((s = grow(h, &h->xbuf, &h->xbuf_bytes, 2 * (size_t)chunk * row_bytes, "staging buffers")) != MRNMF_OK)
+        return s;
+    const size_t nd = (size_t)n * n + n + (size_t)kk * n + (size_t)r * n + 2 + r;
+    if ((s = grow(h, (void**)&h->dout, &h->dout_bytes, 8 * nd + 64, "device outputs")) != MRNMF_OK) return s;
+    double* dR = h->dout;
+    double* dcs = dR + (size_t)n * n;
+    double* dGX = dcs + n;
+    double* dH = dGX + (size_t)kk * n;
+    double* dres = dH + (size_t)r * n;
+    int32_t* dK = reinterpret_cast<int32_t*>(dres + 2);
+
+    if ((s = mrnmf_stream_begin(h, n, MRNMF_F32, prec, kk, seed, stream)) != MRNMF_OK) return s;
+    // the staging buffers start free: mark them done on the compute stream
+    for (int i = 0; i < 2; ++i)
+        if ((e = cudaEventRecord(h->ev_done[i], st)) != cudaSuccess) return cuda_fail(h, e, "event");
+    char* xb = static_cast<char*>(h->xbuf);
+    int q = 0;
+    for (int64_t r0 = 0; r0 < m; r0 += chunk, q ^= 1) {
+        const int64_t rows = std::min(chunk, m - r0);
+        char* dst = xb + (size_t)q * chunk * row_bytes;
+        if ((e = cudaStreamWaitEvent(h->copy_stream, h->ev_done[q], 0)) != cudaSuccess) return cuda_fail(h, e, "wait");
+        if (ldx == n)
+            e = cudaMemcpyAsync(dst, X + r0 * ldx, (size_t)rows * row_bytes, cudaMemcpyHostToDevice, h->copy_stream);
+        else
+            e = cudaMemcpy2DAsync(dst, row_bytes, X + r0 * ldx, ldx * 4, row_bytes, rows, cudaMemcpyHostToDevice,
+                                  h->copy_stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "H2D copy");
+        if ((e = cudaEventRecord(h->ev_copied[q], h->copy_stream)) != cudaSuccess) return cuda_fail(h, e, "event");
+        if ((e = cudaStreamWaitEvent(st, h->ev_copied[q], 0)) != cudaSuccess) return cuda_fail(h, e, "wait");
+        if ((s = mrnmf_stream_push(h, dst, rows, n, stream)) != MRNMF_OK) return s;
+        if ((e = cudaEventRecord(h->ev_done[q], st)) != cudaSuccess) return cuda_fail(h, e, "event");
+    }
+    if ((s = mrnmf_stream_end(h, dR, dcs, kk ? dGX : nullptr, stream)) != MRNMF_OK) return s;
+    if ((s = mrnmf_select_extreme(h, method, dR, n, dcs, kk ? dGX : nullptr, kk, r, dK, nullptr, stream)) != MRNMF_OK)
+        return s;
+    if ((s = mrnmf_nnls_h(h, dR, n, dK, r, dH, stream)) != MRNMF_OK) return s;
+    if ((s = mrnmf_residual(h, dR, n, dK, r, dH, dres, stream)) != MRNMF_OK) return s;
+    if ((e = cudaMemcpyAsync(K, dK, 4 * (size_t)r, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(H, dH, 8 * (size_t)r * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(resid, dres, 16, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(h, e, "D2H copy");
+    if (R && (e = cudaMemcpyAsync(R, dR, 8 * (size_t)n * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(h, e, "D2H copy");
+    return mrnmf_sync_status(h, stream);
+}
+
+mrnmf_status mrnmf_profile_events(mrnmf_handle* h, void* ev_start, void* ev_stop)
+{
+    if (!h) return MRNMF_ERR_INVALID_ARG;
+    if ((ev_start == nullptr) != (ev_stop == nullptr))
+        return fail(h, MRNMF_ERR_INVALID_ARG, "give both events or neither");
+    h->prof_start = static_cast<cudaEvent_t>(ev_start);
+    h->prof_stop = static_cast<cudaEvent_t>(ev_stop);
+    h->st.ev_leaf_start = h->prof_start;
+    h->st.ev_leaf_stop = h->prof_stop;
+    return MRNMF_OK;
+}
+
+uint64_t mrnmf_kernel_launches(void)
+{
+    return mrnmf::g_launches.load();
+}
+
+}  // extern "C"

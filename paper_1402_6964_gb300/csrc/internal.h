@@ -1,0 +1,71 @@
+// internal.h -- host-side interfaces between the C ABI (api.cu) and the
+// kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <atomic>
+
+namespace mrnmf {
+
+// Kernels launched by this library (mrnmf_kernel_launches).
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Running state of one pass: P independent row streams ("mappers" of
+// Sec. 3.5), each with its own n-by-n triangle and its partial column sums
+// and Gaussian projection.
+struct PassState {
+    int n = 0;
+    int k = 0;          // Gaussian rows (0 = no projection)
+    int P = 0;          // number of streams (CTAs of the leaf kernel)
+    int fp64 = 0;       // 1: triangles and reflectors in binary64, else binary32
+    int tc = 0;         // 1: tensor-core (TF32x3) leaf
+    void* R = nullptr;      // P * n * n (dense row-major, zeros below diag), T = float or double
+    void* Rtmp = nullptr;   // ceil(P/2) * n * n, ping-pong buffer of the tree
+    double* cs = nullptr;   // P * n partial column sums
+    double* gx = nullptr;   // P * k * n partial projections
+    uint64_t seed = 0;
+    int64_t rows_seen = 0;  // global row index of the next row (Gaussian key)
+    cudaEvent_t ev_leaf_start = nullptr;  // optional timing events around the leaf kernel
+    cudaEvent_t ev_leaf_stop = nullptr;
+};
+
+size_t pass_state_bytes(int n, int k, int P, int fp64);
+void pass_state_carve(PassState& st, void* base);
+
+// Number of streams for a pass over about `m` rows (0 = unknown / streaming).
+int choose_streams(int n, int k, int fp64, int tc, int64_t m);
+
+// Zero the state (triangles and partials) for a new pass.
+cudaError_t pass_reset(const PassState& st, cudaStream_t s);
+
+// Fold `rows` rows of X (row-major, ldx) into the state.  xf64: X is binary64.
+// qr = 0 skips the triangle (Gaussian projection / column sums only).
+cudaError_t pass_push(PassState& st, const void* X, int64_t rows, int64_t ldx, int xf64, int qr,
+                      int* status, cudaStream_t s);
+
+// Reduce the P triangles to one (tree over the stacked R's, Sec. 3.1), then
+// write R (sign-normalised, binary64), colsum and GX (either may be NULL).
+cudaError_t pass_finish(PassState& st, int qr, double* R, double* colsum, double* GX, int* status,
+                        cudaStream_t s);
+
+// ---- the n-by-n separable step (small_step.cu) ----
+size_t small_ws_bytes(int n, int k, int r);
+cudaError_t select_spa(const double* R, int n, const double* colsum, int r, int32_t* K, double* gap,
+                       void* ws, int* status, cudaStream_t s);
+cudaError_t select_xray(const double* R, int n, int r, int32_t* K, double* gap, void* ws, int* status,
+                        cudaStream_t s);
+cudaError_t select_gp(const double* GX, int k, int n, const double* colsum, int r, int32_t* K, double* gap,
+                      void* ws, int* status, cudaStream_t s);
+cudaError_t nnls_h(const double* R, int n, const int32_t* K, int r, double* H, void* ws, int* status,
+                   cudaStream_t s);
+cudaError_t residual(const double* R, int n, const int32_t* K, int r, const double* H, double* out, void* ws,
+                     cudaStream_t s);
+
+// ---- tensor-core leaf (tsqr_tc.cu) ----
+bool tc_supported(int n);
+
+}  // namespace mrnmf

@@ -1,0 +1,633 @@
+// small_step.cu -- the n-by-n separable step on the device, in binary64.
+//
+// Once the pass has produced R (n-by-n) and the column sums, X = X(:,K)H
+// implies R = R(:,K)H (Sec. 2.2), so the extreme columns, the coefficients
+// and the residual are all computed from R:
+//   SPA       Sec. 2.1 (argmax of column 2-norms of R D^-1, then projection)
+//   XRAY      Sec. 2.1 (greedy: argmax ||Res^T R(:,j)|| / ||R(:,j)||)
+//   GP        Sec. 2.3 + Sec. 3.3 (argmax / argmin of the rows of GX D^-1)
+//   NNLS      Sec. 2.4 (Lawson-Hanson active set on the normal equations)
+//   residual  Sec. 2.4 / Sec. 4
+// Ties go to the lowest index.  Work is O(n^2 r) to O(n^3 r): small next to
+// the pass, and on GB300 binary64 runs on few units, so each kernel spreads
+// its columns over threads and blocks.
+
+#include <cfloat>
+#include <climits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace mrnmf {
+
+namespace {
+
+constexpr int kRMax = 64;  // largest r the NNLS scratch is laid out for
+
+// ---------------------------------------------------------------- top-2 argmax
+struct Top2 {
+    double b1;
+    int i1;
+    double b2;
+};
+
+__device__ __forceinline__ Top2 top2_merge(Top2 a, Top2 b)
+{
+    // the better best (lowest index on ties); the second is the larger of the
+    // loser's best and the winner's second
+    const bool a_wins = (a.b1 > b.b1) || (a.b1 == b.b1 && a.i1 < b.i1);
+    Top2 w = a_wins ? a : b, l = a_wins ? b : a;
+    w.b2 = fmax(w.b2, l.b1);
+    return w;
+}
+
+// Block-wide top-2 over one value per thread (score = -inf for excluded).
+__device__ Top2 block_top2(double v, int idx, Top2* sh)
+{
+    Top2 t{v, idx, -INFINITY};
+    for (int o = 16; o; o >>= 1) {
+        Top2 u;
+        u.b1 = __shfl_xor_sync(0xffffffffu, t.b1, o);
+        u.i1 = __shfl_xor_sync(0xffffffffu, t.i1, o);
+        u.b2 = __shfl_xor_sync(0xffffffffu, t.b2, o);
+        t = top2_merge(t, u);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[w] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Top2 acc = sh[0];
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) acc = top2_merge(acc, sh[q]);
+        sh[0] = acc;
+    }
+    __syncthreads();
+    Top2 r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double pick_gap(const Top2& t)
+{
+    if (t.i1 < 0 || t.b1 == -INFINITY) return -1.0;
+    if (t.b2 == -INFINITY) return 1.0;
+    return t.b1 > 0.0 ? (t.b1 - t.b2) / t.b1 : 0.0;
+}
+
+// ------------------------------------------------------------------------ SPA
+// One CTA; thread j owns column j of Y = R D^-1 (global scratch, row-major).
+__global__ void __launch_bounds__(256) spa_kernel(const double* __restrict__ R, int n, const double* __restrict__ colsum,
+                                                  int r, int32_t* __restrict__ K, double* __restrict__ gap,
+                                                  double* __restrict__ Y, int* status)
+{
+    __shared__ Top2 sh[8];
+    __shared__ double u[MRNMF_NMAX];
+    __shared__ int chosen[MRNMF_NMAX];
+    __shared__ double s_nrm, s_f0;
+    __shared__ int s_p;
+    const int j = threadIdx.x;
+    const bool own = j < n;
+    if (own) {
+        chosen[j] = 0;
+        const double d = colsum[j];
+        for (int i = 0; i < n; ++i) Y[(size_t)i * n + j] = R[(size_t)i * n + j] / d;
+    }
+    __syncthreads();
+    for (int t = 0; t < r; ++t) {
+        double f = -INFINITY;
+        if (own && !chosen[j]) {
+            double s = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const double y = Y[(size_t)i * n + j];
+                s += y * y;
+            }
+            f = s;
+        }
+        const Top2 b = block_top2(f, own && !chosen[j] ? j : INT_MAX, sh);
+        if (j == 0) {
+            const int p = b.i1;
+            if (t == 0) s_f0 = b.b1;
+            double g = pick_gap(b);
+            if (!(b.b1 > 1e-24 * s_f0)) g = -1.0;
+            K[t] = p;
+            if (gap) gap[t] = g;
+            chosen[p] = 1;
+            s_p = p;
+            s_nrm = sqrt(b.b1);
+        }
+        __syncthreads();
+        const int p = s_p;
+        const double nrm = s_nrm;
+        if (!(nrm > 0.0)) continue;
+        if (own) u[j] = Y[(size_t)j * n + p] / nrm;
+        __syncthreads();
+        if (own) {
+            double cj = 0.0;
+            for (int i = 0; i < n; ++i) cj += u[i] * Y[(size_t)i * n + j];
+            for (int i = 0; i < n; ++i) Y[(size_t)i * n + j] -= cj * u[i];
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------- NNLS
+// Normal equations: AtA (r x r), Atb (r x n), btb (n) from R and K.
+__global__ void nnls_gram_kernel(const double* __restrict__ R, int n, const int32_t* __restrict__ K, int r,
+                                 double* __restrict__ AtA, double* __restrict__ Atb, double* __restrict__ btb)
+{
+    const int total = r * r + r * n + n;
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < total; o += gridDim.x * blockDim.x) {
+        int ca, cb;
+        double* dst;
+        if (o < r * r) {
+            ca = K[o / r];
+            cb = K[o % r];
+            dst = AtA + o;
+        } else if (o < r * r + r * n) {
+            const int q = o - r * r;
+            ca = K[q / n];
+            cb = q % n;
+            dst = Atb + q;
+        } else {
+            ca = cb = o - r * r - r * n;
+            dst = btb + ca;
+        }
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += R[(size_t)i * n + ca] * R[(size_t)i * n + cb];
+        *dst = s;
+    }
+}
+
+// Solve AtA[idx,idx] z = rhs[idx] by Cholesky (L: p x p scratch). Returns false
+// if the passive block is not positive definite.
+__device__ bool chol_solve(const double* AtA, int r, const double* rhs, const int* idx, int p, double* L, double* y,
+                           double* z)
+{
+    for (int i = 0; i < p; ++i) {
+        for (int jj = 0; jj <= i; ++jj) {
+            double s = AtA[idx[i] * r + idx[jj]];
+            for (int q = 0; q < jj; ++q) s -= L[i * p + q] * L[jj * p + q];
+            if (i == jj) {
+                if (!(s > 0.0)) return false;
+                L[i * p + i] = sqrt(s);
+            } else {
+                L[i * p + jj] = s / L[jj * p + jj];
+            }
+        }
+    }
+    for (int i = 0; i < p; ++i) {
+        double s = rhs[idx[i]];
+        for (int q = 0; q < i; ++q) s -= L[i * p + q] * y[q];
+        y[i] = s / L[i * p + i];
+    }
+    for (int i = p - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int q = i + 1; q < p; ++q) s -= L[q * p + i] * z[q];
+        z[i] = s / L[i * p + i];
+    }
+    return true;
+}
+
+// Lawson-Hanson, one thread per column c of H.  Per-thread scratch in global
+// memory: L (r*r), y, z, zp, w, x (r each), passive/idx (r ints).
+__global__ void nnls_lh_kernel(const double* __restrict__ AtA, const double* __restrict__ Atb,
+                               const double* __restrict__ btb, int r, int n, double* __restrict__ H,
+                               double* __restrict__ scratch, int* __restrict__ iscratch, int* status)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    double* L = scratch + (size_t)c * (r * r + 6 * r);
+    double* y = L + r * r;
+    double* z = y + r;
+    double* zp = z + r;
+    double* w = zp + r;
+    double* x = w + r;
+    int* passive = iscratch + (size_t)c * 2 * r;
+    int* idx = passive + r;
+    double maxdiag = 0.0;
+    for (int i = 0; i < r; ++i) {
+        x[i] = 0.0;
+        passive[i] = 0;
+        maxdiag = fmax(maxdiag, AtA[i * r + i]);
+    }
+    const double bb = btb[c];
+    const double tol = 1e-12 * sqrt(maxdiag * (bb > 0.0 ? bb : 0.0));
+    int outer = 0;
+    int st = 0;
+    for (;;) {
+        for (int i = 0; i < r; ++i) {
+            double s = Atb[(size_t)i * n + c];
+            for (int q = 0; q < r; ++q) s -= AtA[i * r + q] * x[q];
+            w[i] = s;
+        }
+        int t = -1;
+        double wmax = tol;
+        for (int i = 0; i < r; ++i)
+            if (!passive[i] && w[i] > wmax) {
+                wmax = w[i];
+                t = i;
+            }
+        if (t < 0) break;
+        if (outer >= 3 * r) {
+            st = MRNMF_ERR_NOT_CONVERGED;
+            break;
+        }
+        ++outer;
+        passive[t] = 1;
+        // right-hand side of column c, contiguous (reuse w: it is recomputed next outer step)
+        for (int i = 0; i < r; ++i) w[i] = Atb[(size_t)i * n + c];
+        for (int inner = 0; inner <= r + 1; ++inner) {
+            int p = 0;
+            for (int i = 0; i < r; ++i)
+                if (passive[i]) idx[p++] = i;
+            if (!chol_solve(AtA, r, w, idx, p, L, y, zp)) {
+                st = MRNMF_ERR_RANK_DEFICIENT;
+                goto done;
+            }
+            for (int i = 0; i < r; ++i) z[i] = 0.0;
+            bool allpos = true;
+            for (int q = 0; q < p; ++q) {
+                z[idx[q]] = zp[q];
+                if (zp[q] <= 0.0) allpos = false;
+            }
+            if (allpos) {
+                for (int i = 0; i < r; ++i) x[i] = z[i];
+                break;
+            }
+            double alpha = 2.0;
+            int blocking = -1;
+            for (int q = 0; q < p; ++q) {
+                const int i = idx[q];
+                if (z[i] <= 0.0) {
+                    const double den = x[i] - z[i];  // >= 0; 0 only if x_i = z_i = 0
+                    const double a = den > 0.0 ? x[i] / den : 0.0;
+                    if (a < alpha) {
+                        alpha = a;
+                        blocking = i;
+                    }
+                }
+            }
+            for (int i = 0; i < r; ++i) x[i] += alpha * (z[i] - x[i]);
+            x[blocking] = 0.0;
+            for (int q = 0; q < p; ++q) {
+                const int i = idx[q];
+                if (x[i] <= 0.0) {
+                    passive[i] = 0;
+                    x[i] = 0.0;
+                }
+            }
+            if (inner == r + 1) {
+                st = MRNMF_ERR_NOT_CONVERGED;
+                goto done;
+            }
+        }
+    }
+done:
+    if (st) set_status(status, st);
+    for (int i = 0; i < r; ++i) H[(size_t)i * n + c] = x[i];
+}
+
+// ------------------------------------------------------------------- residual
+// Per-block partial sums of ||R - R(:,K)H||^2 and ||R||^2.
+__global__ void residual_partial_kernel(const double* __restrict__ R, int n, const int32_t* __restrict__ K, int r,
+                                        const double* __restrict__ H, double* __restrict__ part)
+{
+    __shared__ double se[8], sr[8];
+    double e2 = 0.0, r2 = 0.0;
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o < n * n) {
+        const int i = o / n, c = o - i * n;
+        const double v = R[o];
+        double s = v;
+        for (int a = 0; a < r; ++a) s -= R[(size_t)i * n + K[a]] * H[(size_t)a * n + c];
+        e2 = s * s;
+        r2 = v * v;
+    }
+    e2 = warp_sum(e2);
+    r2 = warp_sum(r2);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        se[w] = e2;
+        sr[w] = r2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            a += se[q];
+            b += sr[q];
+        }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void residual_final_kernel(const double* __restrict__ part, int nb, double* __restrict__ out)
+{
+    double a = 0.0, b = 0.0;
+    for (int q = threadIdx.x; q < nb; q += 32) {
+        a += part[2 * q];
+        b += part[2 * q + 1];
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (threadIdx.x == 0) {
+        out[0] = sqrt(a);
+        out[1] = b > 0.0 ? a / b : 0.0;
+    }
+}
+
+// ----------------------------------------------------------------------- XRAY
+// score_j = ||Res^T R(:,j)|| / ||R(:,j)|| for unchosen j (one block per j).
+__global__ void __launch_bounds__(256) xray_score_kernel(const double* __restrict__ R, const double* __restrict__ Res,
+                                                         int n, const int* __restrict__ chosen,
+                                                         double* __restrict__ score)
+{
+    __shared__ double sh[8];
+    const int j = blockIdx.x;
+    if (chosen[j]) {
+        if (threadIdx.x == 0) score[j] = -INFINITY;
+        return;
+    }
+    double acc = 0.0, cn = 0.0;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        double v = 0.0;
+        for (int i = 0; i < n; ++i) v += Res[(size_t)i * n + q] * R[(size_t)i * n + j];
+        acc += v * v;
+    }
+    if (threadIdx.x < 32) {
+        for (int i = threadIdx.x; i < n; i += 32) {
+            const double x = R[(size_t)i * n + j];
+            cn += x * x;
+        }
+        cn = warp_sum(cn);
+    }
+    acc = warp_sum(acc);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[w] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += sh[q];
+        const double nrm = sqrt(cn);
+        score[j] = nrm > 0.0 ? sqrt(s) / nrm : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(256) xray_pick_kernel(const double* __restrict__ score, int n, int t,
+                                                        int* __restrict__ chosen, int32_t* __restrict__ K,
+                                                        double* __restrict__ gap, double* __restrict__ s0)
+{
+    __shared__ Top2 sh[8];
+    double v = -INFINITY;
+    int idx = INT_MAX;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        if (!chosen[j]) {
+            const double s = score[j];
+            if (idx == INT_MAX || s > v) {
+                v = s;
+                idx = j;
+            }
+        }
+    }
+    // second-best within the thread's own strided set is folded by the block merge
+    Top2 b = block_top2(v, idx, sh);
+    if (threadIdx.x == 0) {
+        // the strided pre-pass may hide a per-thread runner-up; recompute the
+        // runner-up exactly
+        double second = -INFINITY;
+        for (int j = 0; j < n; ++j)
+            if (!chosen[j] && j != b.i1) second = fmax(second, score[j]);
+        b.b2 = second;
+        if (t == 0) *s0 = b.b1;
+        double g = pick_gap(b);
+        if (!(b.b1 > 1e-12 * (*s0))) g = -1.0;
+        K[t] = b.i1;
+        if (gap) gap[t] = g;
+        chosen[b.i1] = 1;
+    }
+}
+
+// Res = R - R(:,K) H (t = number of columns in K)
+__global__ void xray_res_kernel(const double* __restrict__ R, int n, const int32_t* __restrict__ K, int t,
+                                const double* __restrict__ H, double* __restrict__ Res)
+{
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n * n) return;
+    const int i = o / n, c = o - i * n;
+    double s = R[o];
+    for (int a = 0; a < t; ++a) s -= R[(size_t)i * n + K[a]] * H[(size_t)a * n + c];
+    Res[o] = s;
+}
+
+__global__ void init_xray_kernel(const double* __restrict__ R, int n, double* __restrict__ Res, int* __restrict__ chosen)
+{
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o < n * n) Res[o] = R[o];
+    if (o < n) chosen[o] = 0;
+}
+
+// ------------------------------------------------------------------------- GP
+// One CTA.  Rows of Z = GX D^-1 are scanned by warps; thread 0 then walks the
+// rows in order, appending argmax then argmin and skipping duplicates.
+__global__ void __launch_bounds__(256) gp_select_kernel(const double* __restrict__ GX, int k, int n,
+                                                        const double* __restrict__ colsum, int r,
+                                                        int32_t* __restrict__ K, double* __restrict__ gap,
+                                                        int* status)
+{
+    __shared__ int jmax_s[MRNMF_KMAX], jmin_s[MRNMF_KMAX];
+    __shared__ double gmax_s[MRNMF_KMAX], gmin_s[MRNMF_KMAX];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int l = warp; l < k; l += blockDim.x >> 5) {
+        double zmax = -INFINITY, zmin = INFINITY, scale = 0.0;
+        int imax = INT_MAX, imin = INT_MAX;
+        for (int j = lane; j < n; j += 32) {
+            const double z = GX[(size_t)l * n + j] / colsum[j];
+            if (z > zmax) {
+                zmax = z;
+                imax = j;
+            }
+            if (z < zmin) {
+                zmin = z;
+                imin = j;
+            }
+            scale = fmax(scale, fabs(z));
+        }
+        for (int o = 16; o; o >>= 1) {
+            const double z2 = __shfl_xor_sync(0xffffffffu, zmax, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, imax, o);
+            if (z2 > zmax || (z2 == zmax && i2 < imax)) {
+                zmax = z2;
+                imax = i2;
+            }
+            const double w2 = __shfl_xor_sync(0xffffffffu, zmin, o);
+            const int k2 = __shfl_xor_sync(0xffffffffu, imin, o);
+            if (w2 < zmin || (w2 == zmin && k2 < imin)) {
+                zmin = w2;
+                imin = k2;
+            }
+            scale = fmax(scale, __shfl_xor_sync(0xffffffffu, scale, o));
+        }
+        double s2max = -INFINITY, s2min = INFINITY;
+        for (int j = lane; j < n; j += 32) {
+            const double z = GX[(size_t)l * n + j] / colsum[j];
+            if (j != imax) s2max = fmax(s2max, z);
+            if (j != imin) s2min = fmin(s2min, z);
+        }
+        for (int o = 16; o; o >>= 1) {
+            s2max = fmax(s2max, __shfl_xor_sync(0xffffffffu, s2max, o));
+            s2min = fmin(s2min, __shfl_xor_sync(0xffffffffu, s2min, o));
+        }
+        if (lane == 0) {
+            jmax_s[l] = imax;
+            jmin_s[l] = imin;
+            gmax_s[l] = (n > 1 && scale > 0.0) ? (zmax - s2max) / scale : 1.0;
+            gmin_s[l] = (n > 1 && scale > 0.0) ? (s2min - zmin) / scale : 1.0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int cnt = 0;
+        for (int l = 0; l < k && cnt < r; ++l) {
+            const int picks[2] = {jmax_s[l], jmin_s[l]};
+            const double pg[2] = {gmax_s[l], gmin_s[l]};
+            for (int q = 0; q < 2 && cnt < r; ++q) {
+                bool dup = false;
+                for (int c = 0; c < cnt; ++c)
+                    if (K[c] == picks[q]) dup = true;
+                if (!dup) {
+                    if (gap) gap[cnt] = pg[q];
+                    K[cnt++] = picks[q];
+                }
+            }
+        }
+        for (int t = cnt; t < r; ++t) {
+            K[t] = -1;
+            if (gap) gap[t] = -1.0;
+        }
+        if (cnt < r) set_status(status, MRNMF_ERR_RANK_DEFICIENT);
+    }
+}
+
+// Workspace layout of the small step.
+struct SmallWs {
+    double* Y;      // n*n (SPA)        / Res (XRAY)
+    double* Hs;     // r*n (XRAY inner H)
+    double* AtA;    // r*r
+    double* Atb;    // r*n
+    double* btb;    // n
+    double* score;  // n
+    double* part;   // 2*ceil(n*n/256)
+    double* s0;     // 1
+    double* nnls;   // n*(r*r + 6r)
+    int* chosen;    // n
+    int* inls;      // n*2r
+};
+
+size_t a16(size_t b) { return (b + 15) & ~size_t(15); }
+
+SmallWs carve(void* ws, int n, int r)
+{
+    SmallWs w;
+    char* p = static_cast<char*>(ws);
+    auto take = [&](size_t bytes) {
+        char* q = p;
+        p += a16(bytes);
+        return q;
+    };
+    w.Y = (double*)take(8ull * n * n);
+    w.Hs = (double*)take(8ull * r * n);
+    w.AtA = (double*)take(8ull * r * r);
+    w.Atb = (double*)take(8ull * r * n);
+    w.btb = (double*)take(8ull * n);
+    w.score = (double*)take(8ull * n);
+    w.part = (double*)take(8ull * 2 * ((n * n + 255) / 256));
+    w.s0 = (double*)take(16);
+    w.nnls = (double*)take(8ull * n * (r * r + 6 * r));
+    w.chosen = (int*)take(4ull * n);
+    w.inls = (int*)take(4ull * n * 2 * r);
+    return w;
+}
+
+cudaError_t nnls_core(const double* R, int n, const int32_t* K, int r, double* H, const SmallWs& w, int* status,
+                      cudaStream_t s)
+{
+    const int total = r * r + r * n + n;
+    nnls_gram_kernel<<<(total + 127) / 128, 128, 0, s>>>(R, n, K, r, w.AtA, w.Atb, w.btb);
+    count_launch();
+    nnls_lh_kernel<<<(n + 31) / 32, 32, 0, s>>>(w.AtA, w.Atb, w.btb, r, n, H, w.nnls, w.inls, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t small_ws_bytes(int n, int k, int r)
+{
+    (void)k;
+    if (r < 1) r = 1;
+    size_t b = 0;
+    b += a16(8ull * n * n) + a16(8ull * r * n) + a16(8ull * r * r) + a16(8ull * r * n);
+    b += a16(8ull * n) * 2 + a16(8ull * 2 * ((n * n + 255) / 256)) + a16(16);
+    b += a16(8ull * n * (r * r + 6 * r)) + a16(4ull * n) + a16(4ull * n * 2 * r);
+    return b;
+}
+
+cudaError_t select_spa(const double* R, int n, const double* colsum, int r, int32_t* K, double* gap, void* ws,
+                       int* status, cudaStream_t s)
+{
+    SmallWs w = carve(ws, n, r);
+    spa_kernel<<<1, ((n + 31) / 32) * 32, 0, s>>>(R, n, colsum, r, K, gap, w.Y, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t select_xray(const double* R, int n, int r, int32_t* K, double* gap, void* ws, int* status,
+                        cudaStream_t s)
+{
+    if (r > kRMax) return cudaErrorInvalidValue;
+    SmallWs w = carve(ws, n, r);
+    init_xray_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(R, n, w.Y, w.chosen);
+    count_launch();
+    for (int t = 0; t < r; ++t) {
+        xray_score_kernel<<<n, 128, 0, s>>>(R, w.Y, n, w.chosen, w.score);
+        count_launch();
+        xray_pick_kernel<<<1, 256, 0, s>>>(w.score, n, t, w.chosen, K, gap, w.s0);
+        count_launch();
+        cudaError_t e = nnls_core(R, n, K, t + 1, w.Hs, w, status, s);
+        if (e != cudaSuccess) return e;
+        xray_res_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(R, n, K, t + 1, w.Hs, w.Y);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t select_gp(const double* GX, int k, int n, const double* colsum, int r, int32_t* K, double* gap,
+                      void* ws, int* status, cudaStream_t s)
+{
+    (void)ws;
+    gp_select_kernel<<<1, 256, 0, s>>>(GX, k, n, colsum, r, K, gap, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t nnls_h(const double* R, int n, const int32_t* K, int r, double* H, void* ws, int* status,
+                   cudaStream_t s)
+{
+    if (r > kRMax) return cudaErrorInvalidValue;
+    SmallWs w = carve(ws, n, r);
+    return nnls_core(R, n, K, r, H, w, status, s);
+}
+
+cudaError_t residual(const double* R, int n, const int32_t* K, int r, const double* H, double* out, void* ws,
+                     cudaStream_t s)
+{
+    SmallWs w = carve(ws, n, r);
+    const int nb = (n * n + 255) / 256;
+    residual_partial_kernel<<<nb, 256, 0, s>>>(R, n, K, r, H, w.part);
+    count_launch();
+    residual_final_kernel<<<1, 32, 0, s>>>(w.part, nb, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace mrnmf

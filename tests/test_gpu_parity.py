@@ -1,0 +1,324 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (stated once, used below):
+  R, FP32 pass : ||R_gpu - R_orc||_F / ||R_orc||_F <= 1e-5  (target fixed for the FP32 form)
+  R, FP64 pass : <= 1e-12
+  colsum       : relative 1e-6 (FP32 pass; binary32 tile sums, binary64 across tiles)
+  GX           : |GX_gpu - GX_orc| <= 2e-6 * (|G|^T |X|) elementwise, the natural bound of
+                 a binary32 sum of products (G drawn in binary32 on the device)
+  H, residual  : relative 1e-4 when K matches (spec bound); 1e-9 on identical inputs
+  K            : bit-exact at every pick whose relative gap exceeds the margin
+                 (100x the pass's R error); smaller gaps are tie-ambiguous and only the
+                 validity of the pick is checked.
+"""
+import numpy as np
+import pytest
+
+from paper_1402_6964_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+R_TOL_FP32 = 1e-5
+MARGIN = 1e-3
+
+
+@pytest.fixture(scope="module")
+def h():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_6964_gb300 import build, mrnmf
+    build.build()
+    hd = mrnmf.Handle()
+    yield hd
+    hd.close()
+
+
+def rel_fro(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def compare_K(Kg, Ko, gap, margin=MARGIN):
+    """K equal at every step whose oracle gap is above the margin; afterwards
+    (once a pick was ambiguous) the sequences may legitimately diverge."""
+    for t in range(len(Ko)):
+        if gap[t] < margin:
+            return t
+        assert Kg[t] == Ko[t], f"pick {t}: gpu {Kg[t]} vs oracle {Ko[t]} (gap {gap[t]:.3g})"
+    return len(Ko)
+
+
+# --------------------------------------------------------------------- R
+
+SHAPES = [(1, 1), (5, 5), (17, 3), (33, 32), (1000, 1), (1000, 7), (4099, 20), (12345, 50),
+          (5000, 64), (3001, 65), (20000, 128), (7001, 200), (3000, 256)]
+
+
+@pytest.mark.parametrize("m,n", SHAPES)
+def test_tsqr_fp32_matches_oracle(h, oracle, m, n):
+    X = synth.random_nonneg(m, n, seed=m * 1000 + n)
+    R, cs = h.tsqr_r(dev(X), prec="fp32")
+    h.sync()
+    Ro = oracle.qr_r(X.astype(np.float64))
+    Rg = host(R)
+    assert np.all(np.tril(Rg, -1) == 0) and np.all(np.diag(Rg) >= 0)
+    assert rel_fro(Rg, Ro) <= R_TOL_FP32
+    np.testing.assert_allclose(host(cs), oracle.colsum(X.astype(np.float64)), rtol=1e-6)
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (37, 20), (20000, 20), (9999, 64), (4000, 128)])
+def test_tsqr_fp64_matches_oracle(h, oracle, m, n):
+    X = synth.random_nonneg(m, n, seed=77 + n, dtype=np.float64)
+    R, cs = h.tsqr_r(dev(X), prec="fp64")
+    h.sync()
+    assert rel_fro(host(R), oracle.qr_r(X)) <= 1e-12
+    np.testing.assert_allclose(host(cs), oracle.colsum(X), rtol=1e-13)
+
+
+def test_tsqr_strided_rows(h, oracle):
+    # ldx > n: X is a column slice of a wider row-major array
+    W = synth.random_nonneg(3000, 40, seed=5)
+    Xd = dev(W)[:, 3:33]
+    R, _ = h.tsqr_r(Xd, prec="fp32")
+    h.sync()
+    assert rel_fro(host(R), oracle.qr_r(W[:, 3:33].astype(np.float64))) <= R_TOL_FP32
+
+
+def test_tsqr_ill_conditioned(h, oracle):
+    # column scaling 10^U(0,6) (cond ~ 1e6): R per column relative error stays
+    # at the FP32 backward-error level scaled by each column's size
+    X, P = synth.planted_separable(200000, 40, 8, seed=1402003, noise=1e-3, decades=6.0)
+    R, _ = h.tsqr_r(dev(X), prec="fp32")
+    h.sync()
+    Ro = oracle.qr_r(X.astype(np.float64))
+    Rg = host(R)
+    assert rel_fro(Rg, Ro) <= R_TOL_FP32
+    col = np.linalg.norm(Rg - Ro, axis=0) / np.linalg.norm(Ro, axis=0)
+    assert np.max(col) < 1e-3
+
+
+def test_bad_input_is_reported(h):
+    from paper_1402_6964_gb300 import mrnmf
+    X = synth.random_nonneg(500, 6, seed=1)
+    for mutate in ("neg", "nan", "zerocol"):
+        Y = X.copy()
+        if mutate == "neg":
+            Y[123, 4] = -1e-3
+        elif mutate == "nan":
+            Y[77, 2] = np.nan
+        else:
+            Y[:, 3] = 0.0
+        h.tsqr_r(dev(Y), prec="fp32")
+        with pytest.raises(mrnmf.MrnmfError) as e:
+            h.sync()
+        assert e.value.status == mrnmf.ERR_BAD_INPUT
+    # the handle stays usable afterwards
+    h.tsqr_r(dev(X), prec="fp32")
+    h.sync()
+
+
+# -------------------------------------------------------------------- GX
+
+def _gx_bound(X, k, seed, row0=0):
+    import oracle as orc
+    G = orc.gauss_matrix(seed, row0, X.shape[0], k)
+    return np.abs(G).T @ np.abs(X.astype(np.float64))
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (1000, 7, 3), (4099, 20, 10), (30011, 50, 20), (5000, 128, 64)])
+def test_gauss_project_matches_oracle(h, oracle, m, n, k):
+    X = synth.random_nonneg(m, n, seed=m + n + k)
+    GX, cs = h.gauss_project(dev(X), k, seed=1234567, row_offset=0)
+    h.sync()
+    GXo = oracle.gauss_project(X.astype(np.float64), k, 1234567)
+    assert np.all(np.abs(host(GX) - GXo) <= 2e-6 * _gx_bound(X, k, 1234567) + 1e-12)
+    np.testing.assert_allclose(host(cs), oracle.colsum(X.astype(np.float64)), rtol=1e-6)
+
+
+def test_gauss_project_row_offset(h, oracle):
+    X = synth.random_nonneg(3000, 9, seed=9)
+    GX, _ = h.gauss_project(dev(X), 6, seed=42, row_offset=10_000_000_000)
+    h.sync()
+    GXo = oracle.gauss_project(X.astype(np.float64), 6, 42, row0=10_000_000_000)
+    assert np.all(np.abs(host(GX) - GXo) <= 2e-6 * _gx_bound(X, 6, 42, 10_000_000_000) + 1e-12)
+
+
+def test_fused_pass_matches_separate(h, oracle):
+    # Sec. 3.5: TSQR and GP in one pass give what the two separate passes give
+    X = synth.random_nonneg(20011, 30, seed=3)
+    R, cs, GX = h.tsqr_gp(dev(X), 12, seed=99, prec="fp32")
+    h.sync()
+    Ro = oracle.qr_r(X.astype(np.float64))
+    assert rel_fro(host(R), Ro) <= R_TOL_FP32
+    GXo = oracle.gauss_project(X.astype(np.float64), 12, 99)
+    assert np.all(np.abs(host(GX) - GXo) <= 2e-6 * _gx_bound(X, 12, 99) + 1e-12)
+
+
+# ---------------------------------------------- the n-by-n step, same inputs
+
+@pytest.fixture(scope="module")
+def reduced(oracle):
+    X, P = synth.planted_separable(60000, 48, 9, seed=21, noise=1e-3)
+    X64 = X.astype(np.float64)
+    return X, P, oracle.qr_r(X64), oracle.colsum(X64), oracle.gauss_project(X64, 18, 5)
+
+
+def test_spa_same_input(h, oracle, reduced):
+    X, P, Ro, so, GXo = reduced
+    K, gap = h.select_extreme("spa", R=dev(Ro), colsum=dev(so), r=9)
+    h.sync()
+    Ko, go = oracle.spa(Ro, so, 9)
+    assert list(host(K)) == list(Ko)
+    np.testing.assert_allclose(host(gap), go, rtol=1e-9, atol=1e-12)
+
+
+def test_xray_same_input(h, oracle, reduced):
+    X, P, Ro, so, GXo = reduced
+    K, gap = h.select_extreme("xray", R=dev(Ro), r=9)
+    h.sync()
+    Ko, go, st = oracle.xray(Ro, 9)
+    assert list(host(K)) == list(Ko)
+    np.testing.assert_allclose(host(gap), go, rtol=1e-8, atol=1e-12)
+
+
+def test_gp_same_input(h, oracle, reduced):
+    X, P, Ro, so, GXo = reduced
+    K, gap = h.select_extreme("gp", colsum=dev(so), GX=dev(GXo), r=9)
+    h.sync()
+    Ko, cand, cg = oracle.gp_select(GXo, so, 9)
+    assert list(host(K)) == list(Ko)
+    np.testing.assert_allclose(host(gap), cg[:9], rtol=1e-9, atol=1e-12)
+
+
+def test_nnls_residual_same_input(h, oracle, reduced):
+    X, P, Ro, so, GXo = reduced
+    K = P.K
+    H = h.nnls_h(dev(Ro), dev(K.astype(np.int32)))
+    out = h.residual(dev(Ro), dev(K.astype(np.int32)), H)
+    h.sync()
+    Ho, st = oracle.nnls_h(Ro, K)
+    assert st == 0
+    np.testing.assert_allclose(host(H), Ho, rtol=1e-9, atol=1e-11)
+    ab, rel = oracle.residual(Ro, K, Ho)
+    o = host(out)
+    assert o[0] == pytest.approx(ab, rel=1e-9) and o[1] == pytest.approx(rel, rel=1e-9)
+
+
+def test_nnls_handles_degenerate_K(h, oracle):
+    # a repeated column makes R(:,K) singular: reported, not hung
+    from paper_1402_6964_gb300 import mrnmf
+    X = synth.random_nonneg(400, 10, seed=8).astype(np.float64)
+    Ro = oracle.qr_r(X)
+    h.nnls_h(dev(Ro), dev(np.array([2, 2, 5], np.int32)))
+    with pytest.raises(mrnmf.MrnmfError) as e:
+        h.sync()
+    assert e.value.status in (mrnmf.ERR_RANK_DEFICIENT, mrnmf.ERR_NOT_CONVERGED)
+
+
+# ----------------------------------------------------------- end to end
+
+def test_exact_separable_fp64_end_to_end(h, oracle):
+    # 20000 x 20, r = 5, FP64: K exact, zero residual (Sec. 4)
+    w = synth.WORKLOADS["exact_fp64"]
+    X, P = synth.workload_matrix(w)
+    R, cs = h.tsqr_r(dev(X), prec="fp64")
+    K, gap = h.select_extreme("spa", R=R, colsum=cs, r=w.r)
+    H = h.nnls_h(R, K)
+    out = h.residual(R, K, H)
+    h.sync()
+    Rg = host(R)
+    np.testing.assert_allclose(Rg.T @ Rg, X.T @ X, rtol=1e-11, atol=1e-9 * np.abs(X.T @ X).max())
+    assert sorted(host(K)) == list(P.K)
+    Ko, _ = oracle.spa(oracle.qr_r(X), oracle.colsum(X), w.r)
+    assert list(host(K)) == list(Ko)
+    assert host(out)[1] < 1e-20
+    order = np.argsort(host(K))
+    np.testing.assert_allclose(host(H)[order], P.H_true, atol=1e-9)
+
+
+@pytest.mark.parametrize("method", ["spa", "xray", "gp"])
+def test_near_separable_end_to_end(h, oracle, method):
+    # near-separable FP32 (sigma = 1e-3), 2e5 x 50, r = 10, k = 20
+    X, P = synth.planted_separable(200000, 50, 10, seed=1402002, noise=1e-3)
+    X64 = X.astype(np.float64)
+    R, cs, GX = h.tsqr_gp(dev(X), 20, seed=7, prec="fp32")
+    K, gap = h.select_extreme(method, R=R, colsum=cs, GX=GX if method == "gp" else None, r=10)
+    H = h.nnls_h(R, K)
+    out = h.residual(R, K, H)
+    h.sync()
+    Ro = oracle.qr_r(X64)
+    so = oracle.colsum(X64)
+    if method == "spa":
+        Ko, go = oracle.spa(Ro, so, 10)
+    elif method == "xray":
+        Ko, go, _ = oracle.xray(Ro, 10)
+    else:
+        Ko, cand, go = oracle.gp_select(oracle.gauss_project(X64, 20, 7), so, 10)
+    Kg = host(K)
+    t = compare_K(Kg, Ko, go)
+    if t == 10:
+        Ho, _ = oracle.nnls_h(Ro, Ko)
+        assert rel_fro(host(H), Ho) <= 1e-4
+        ab, rel = oracle.residual(Ro, Ko, Ho)
+        assert host(out)[0] == pytest.approx(ab, rel=1e-4)
+    if method != "xray":
+        assert sorted(Kg) == list(P.K)  # SPA and GP recover the planted columns (Sec. 4)
+
+
+def test_streaming_matches_one_shot(h, oracle):
+    X = synth.random_nonneg(50000, 24, seed=17)
+    h.stream_begin(24, k=8, seed=3)
+    for a, b in [(0, 1), (1, 4000), (4000, 4001), (4001, 33333), (33333, 50000)]:
+        h.stream_push(dev(X[a:b]))
+    R, cs, GX = h.stream_end(24, k=8)
+    h.sync()
+    X64 = X.astype(np.float64)
+    assert rel_fro(host(R), oracle.qr_r(X64)) <= R_TOL_FP32
+    np.testing.assert_allclose(host(cs), oracle.colsum(X64), rtol=1e-6)
+    GXo = oracle.gauss_project(X64, 8, 3)
+    assert np.all(np.abs(host(GX) - GXo) <= 2e-6 * _gx_bound(X, 8, 3) + 1e-12)
+
+
+def test_factorize_host(h, oracle):
+    X, P = synth.planted_separable(100000, 30, 6, seed=44, noise=1e-3)
+    K, H, res, R = h.factorize_host(X, 6, method="spa", want_R=True)
+    X64 = X.astype(np.float64)
+    Ro = oracle.qr_r(X64)
+    assert rel_fro(R, Ro) <= R_TOL_FP32
+    Ko, go = oracle.spa(Ro, oracle.colsum(X64), 6)
+    assert compare_K(K, Ko, go) == 6
+    Ho, _ = oracle.nnls_h(Ro, Ko)
+    assert rel_fro(H, Ho) <= 1e-4
+    assert sorted(K) == list(P.K)
+
+
+def test_full_size_near_separable(h, oracle):
+    """1e7 x 50 FP32 (the benchmarked workload) in bench.py's launch
+    configuration: R by the Gram identity R^T R = X^T X and against the unique
+    R = chol(X^T X)^T (a library route), colsum, the fused pass's GX against the
+    oracle's row-by-row G^T X, and SPA's K against the oracle's SPA on that R."""
+    w = synth.WORKLOADS["near_sep_1e7x50"]
+    X, P = synth.workload_matrix(w)
+    R, cs, GX = h.tsqr_gp(dev(X), w.k, seed=w.seed, prec="auto")
+    K, gap = h.select_extreme("spa", R=R, colsum=cs, r=w.r)
+    h.sync()
+    Rg = host(R)
+    X64 = X.astype(np.float64)
+    G = X64.T @ X64
+    assert np.linalg.norm(Rg.T @ Rg - G) / np.linalg.norm(G) <= 2 * R_TOL_FP32
+    Rc = np.linalg.cholesky(G).T
+    assert rel_fro(Rg, Rc) <= R_TOL_FP32
+    np.testing.assert_allclose(host(cs), X64.sum(0), rtol=1e-6)
+    GXo = oracle.gauss_project(X64, w.k, w.seed)
+    assert np.all(np.abs(host(GX) - GXo) <= 2e-6 * _gx_bound(X, w.k, w.seed) + 1e-12)
+    Ko, go = oracle.spa(Rc, X64.sum(0), w.r)
+    assert compare_K(host(K), Ko, go) == w.r
+    assert sorted(host(K)) == list(P.K)
