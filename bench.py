@@ -151,7 +151,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     w = synth.WORKLOADS[args.workload]
-    X, P = synth.workload_matrix(w)
+    X, P = synth.workload_matrix(w, m=args.rows)
     m, n, r, k = X.shape[0], w.n, w.r, w.k
     Xd = torch.from_numpy(X).cuda()
     dev = Xd.device
@@ -177,6 +177,9 @@ def run_ours(args):
     h.sync()
 
     leaf_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in leaf_ev:  # torch creates the CUDA event on first record; the library re-records it
+        a.record(stream)
+        b.record(stream)
     step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     clocks = ClockSampler(local)
     if world > 1:
@@ -269,7 +272,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": w.name, "m": m, "n": n, "r": r, "k": k, "prec": args.prec,
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "l2": "input (2.0 GB) larger than L2 (129 MB); no flush needed"},
+                           "l2": f"input ({bytes_step / 1e9:.2f} GB) larger than L2 (129 MB); no flush needed"},
                 "roofline": roofline, "roofline_other": roof_alu if roofline is roof_hbm else roof_hbm,
                 "leaf_ms": statistics.mean(leaf_ms), "r_error": {"rel_fro_vs_chol_gram": r_err},
                 "K_spa": K_spa, "K_planted": P.K.tolist(),
@@ -289,6 +292,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--prec", choices=["auto", "fp32", "tf32x3"], default="auto")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--rows", type=int, default=None, help="first ROWS rows only (profiling a smaller case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=1_000_000)

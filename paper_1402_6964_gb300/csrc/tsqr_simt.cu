@@ -67,7 +67,7 @@ __host__ __device__ inline size_t leaf_smem_bytes(int n)
 }
 
 template <typename TX, typename T, int L, int KMAX, bool QR, bool TRI>
-__global__ void __launch_bounds__(256) leaf_kernel(const LeafArgs a)
+__device__ __forceinline__ void leaf_body(const LeafArgs& a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n;
@@ -246,6 +246,20 @@ __global__ void __launch_bounds__(256) leaf_kernel(const LeafArgs a)
     }
 }
 
+// The pass over X: one CTA per row stream.
+template <typename TX, typename T, int L, int KMAX, bool QR>
+__global__ void __launch_bounds__(256) tsqr_leaf_kernel(const LeafArgs a)
+{
+    leaf_body<TX, T, L, KMAX, QR, false>(a);
+}
+
+// One level of the reduction tree over the stacked triangles.
+template <typename T, int L>
+__global__ void __launch_bounds__(256) tsqr_tree_kernel(const LeafArgs a)
+{
+    leaf_body<T, T, L, 0, true, true>(a);
+}
+
 // R <- sign-normalised binary64 copy of the final triangle (diag >= 0).
 template <typename T>
 __global__ void finalize_r_kernel(const T* __restrict__ Rf, int n, double* __restrict__ R)
@@ -289,7 +303,9 @@ __global__ void reduce_partials_kernel(const double* __restrict__ cs, const doub
 template <typename TX, typename T, int L, int KMAX, bool QR, bool TRI>
 cudaError_t launch_leaf_on(const LeafArgs& a, int grid, cudaStream_t s)
 {
-    auto kern = leaf_kernel<TX, T, L, KMAX, QR, TRI>;
+    void (*kern)(const LeafArgs);
+    if constexpr (TRI) kern = tsqr_tree_kernel<T, L>;
+    else kern = tsqr_leaf_kernel<TX, T, L, KMAX, QR>;
     const size_t smem = leaf_smem_bytes<T, L, KMAX>(a.n);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

