@@ -157,56 +157,68 @@ __global__ void nnls_gram_kernel(const double* __restrict__ R, int n, const int3
     }
 }
 
-// Solve AtA[idx,idx] z = rhs[idx] by Cholesky (L: p x p scratch). Returns false
-// if the passive block is not positive definite.
-__device__ bool chol_solve(const double* AtA, int r, const double* rhs, const int* idx, int p, double* L, double* y,
-                           double* z)
+// Per-column Lawson-Hanson scratch, element e of array x at x[e * S] (S = the
+// interleave stride: 32 columns share a bank-conflict-free shared block, or
+// S = 1 for the global-memory fallback).
+struct LhScratch {
+    double* L;   // r*r Cholesky factor of the passive block
+    double* y;   // r
+    double* z;   // r
+    double* zp;  // r
+    double* w;   // r  (dual, then right-hand side)
+    double* x;   // r  (iterate)
+    int* passive;  // r
+    int* idx;      // r
+    int S;
+};
+
+// Solve AtA[idx,idx] z = rhs[idx] by Cholesky.  Returns false if the passive
+// block is not positive definite.
+__device__ bool chol_solve(const double* AtA, int r, const double* rhs, int S, const int* idx, int p, double* L,
+                           double* y, double* z)
 {
     for (int i = 0; i < p; ++i) {
         for (int jj = 0; jj <= i; ++jj) {
-            double s = AtA[idx[i] * r + idx[jj]];
-            for (int q = 0; q < jj; ++q) s -= L[i * p + q] * L[jj * p + q];
+            double s = AtA[idx[i * S] * r + idx[jj * S]];
+            for (int q = 0; q < jj; ++q) s -= L[(i * p + q) * S] * L[(jj * p + q) * S];
             if (i == jj) {
                 if (!(s > 0.0)) return false;
-                L[i * p + i] = sqrt(s);
+                L[(i * p + i) * S] = sqrt(s);
             } else {
-                L[i * p + jj] = s / L[jj * p + jj];
+                L[(i * p + jj) * S] = s / L[(jj * p + jj) * S];
             }
         }
     }
     for (int i = 0; i < p; ++i) {
-        double s = rhs[idx[i]];
-        for (int q = 0; q < i; ++q) s -= L[i * p + q] * y[q];
-        y[i] = s / L[i * p + i];
+        double s = rhs[idx[i * S] * S];
+        for (int q = 0; q < i; ++q) s -= L[(i * p + q) * S] * y[q * S];
+        y[i * S] = s / L[(i * p + i) * S];
     }
     for (int i = p - 1; i >= 0; --i) {
-        double s = y[i];
-        for (int q = i + 1; q < p; ++q) s -= L[q * p + i] * z[q];
-        z[i] = s / L[i * p + i];
+        double s = y[i * S];
+        for (int q = i + 1; q < p; ++q) s -= L[(q * p + i) * S] * z[q * S];
+        z[i * S] = s / L[(i * p + i) * S];
     }
     return true;
 }
 
-// Lawson-Hanson, one thread per column c of H.  Per-thread scratch in global
-// memory: L (r*r), y, z, zp, w, x (r each), passive/idx (r ints).
-__global__ void nnls_lh_kernel(const double* __restrict__ AtA, const double* __restrict__ Atb,
-                               const double* __restrict__ btb, int r, int n, double* __restrict__ H,
-                               double* __restrict__ scratch, int* __restrict__ iscratch, int* status)
+// Lawson-Hanson on the normal equations for column c (the oracle's steps:
+// add the most positive dual, solve on the passive set, step back to the
+// feasible boundary while any passive coefficient is not positive).
+__device__ void lh_column(const double* AtA, const double* __restrict__ Atb, const double* __restrict__ btb, int r,
+                          int n, int c, const LhScratch& sc, double* __restrict__ H, int* status)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
-    double* L = scratch + (size_t)c * (r * r + 6 * r);
-    double* y = L + r * r;
-    double* z = y + r;
-    double* zp = z + r;
-    double* w = zp + r;
-    double* x = w + r;
-    int* passive = iscratch + (size_t)c * 2 * r;
-    int* idx = passive + r;
+    const int S = sc.S;
+    double* x = sc.x;
+    double* w = sc.w;
+    double* z = sc.z;
+    double* zp = sc.zp;
+    int* passive = sc.passive;
+    int* idx = sc.idx;
     double maxdiag = 0.0;
     for (int i = 0; i < r; ++i) {
-        x[i] = 0.0;
-        passive[i] = 0;
+        x[i * S] = 0.0;
+        passive[i * S] = 0;
         maxdiag = fmax(maxdiag, AtA[i * r + i]);
     }
     const double bb = btb[c];
@@ -216,14 +228,14 @@ __global__ void nnls_lh_kernel(const double* __restrict__ AtA, const double* __r
     for (;;) {
         for (int i = 0; i < r; ++i) {
             double s = Atb[(size_t)i * n + c];
-            for (int q = 0; q < r; ++q) s -= AtA[i * r + q] * x[q];
-            w[i] = s;
+            for (int q = 0; q < r; ++q) s -= AtA[i * r + q] * x[q * S];
+            w[i * S] = s;
         }
         int t = -1;
         double wmax = tol;
         for (int i = 0; i < r; ++i)
-            if (!passive[i] && w[i] > wmax) {
-                wmax = w[i];
+            if (!passive[i * S] && w[i * S] > wmax) {
+                wmax = w[i * S];
                 t = i;
             }
         if (t < 0) break;
@@ -232,47 +244,46 @@ __global__ void nnls_lh_kernel(const double* __restrict__ AtA, const double* __r
             break;
         }
         ++outer;
-        passive[t] = 1;
-        // right-hand side of column c, contiguous (reuse w: it is recomputed next outer step)
-        for (int i = 0; i < r; ++i) w[i] = Atb[(size_t)i * n + c];
+        passive[t * S] = 1;
+        for (int i = 0; i < r; ++i) w[i * S] = Atb[(size_t)i * n + c];  // right-hand side
         for (int inner = 0; inner <= r + 1; ++inner) {
             int p = 0;
             for (int i = 0; i < r; ++i)
-                if (passive[i]) idx[p++] = i;
-            if (!chol_solve(AtA, r, w, idx, p, L, y, zp)) {
+                if (passive[i * S]) idx[(p++) * S] = i;
+            if (!chol_solve(AtA, r, w, S, idx, p, sc.L, sc.y, zp)) {
                 st = MRNMF_ERR_RANK_DEFICIENT;
                 goto done;
             }
-            for (int i = 0; i < r; ++i) z[i] = 0.0;
+            for (int i = 0; i < r; ++i) z[i * S] = 0.0;
             bool allpos = true;
             for (int q = 0; q < p; ++q) {
-                z[idx[q]] = zp[q];
-                if (zp[q] <= 0.0) allpos = false;
+                z[idx[q * S] * S] = zp[q * S];
+                if (zp[q * S] <= 0.0) allpos = false;
             }
             if (allpos) {
-                for (int i = 0; i < r; ++i) x[i] = z[i];
+                for (int i = 0; i < r; ++i) x[i * S] = z[i * S];
                 break;
             }
             double alpha = 2.0;
             int blocking = -1;
             for (int q = 0; q < p; ++q) {
-                const int i = idx[q];
-                if (z[i] <= 0.0) {
-                    const double den = x[i] - z[i];  // >= 0; 0 only if x_i = z_i = 0
-                    const double a = den > 0.0 ? x[i] / den : 0.0;
+                const int i = idx[q * S];
+                if (z[i * S] <= 0.0) {
+                    const double den = x[i * S] - z[i * S];  // >= 0; 0 only if x_i = z_i = 0
+                    const double a = den > 0.0 ? x[i * S] / den : 0.0;
                     if (a < alpha) {
                         alpha = a;
                         blocking = i;
                     }
                 }
             }
-            for (int i = 0; i < r; ++i) x[i] += alpha * (z[i] - x[i]);
-            x[blocking] = 0.0;
+            for (int i = 0; i < r; ++i) x[i * S] += alpha * (z[i * S] - x[i * S]);
+            x[blocking * S] = 0.0;
             for (int q = 0; q < p; ++q) {
-                const int i = idx[q];
-                if (x[i] <= 0.0) {
-                    passive[i] = 0;
-                    x[i] = 0.0;
+                const int i = idx[q * S];
+                if (x[i * S] <= 0.0) {
+                    passive[i * S] = 0;
+                    x[i * S] = 0.0;
                 }
             }
             if (inner == r + 1) {
@@ -283,8 +294,60 @@ __global__ void nnls_lh_kernel(const double* __restrict__ AtA, const double* __r
     }
 done:
     if (st) set_status(status, st);
-    for (int i = 0; i < r; ++i) H[(size_t)i * n + c] = x[i];
+    for (int i = 0; i < r; ++i) H[(size_t)i * n + c] = x[i * S];
 }
+
+// Shared-memory form: 32 columns per block, AtA staged in shared memory, each
+// thread's scratch interleaved with stride 32 (thread t owns element e at
+// [e * 32 + t]) so the 32 threads never hit the same bank.
+__global__ void __launch_bounds__(32) nnls_lh_smem_kernel(const double* __restrict__ AtA_g,
+                                                          const double* __restrict__ Atb,
+                                                          const double* __restrict__ btb, int r, int n,
+                                                          double* __restrict__ H, int* status)
+{
+    extern __shared__ __align__(16) double sm[];
+    double* AtA = sm;
+    double* base = sm + r * r;
+    for (int i = threadIdx.x; i < r * r; i += 32) AtA[i] = AtA_g[i];
+    __syncwarp();
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    if (c >= n) return;
+    LhScratch sc;
+    sc.S = 32;
+    double* mine = base + threadIdx.x;
+    sc.L = mine;
+    sc.y = sc.L + r * r * 32;
+    sc.z = sc.y + r * 32;
+    sc.zp = sc.z + r * 32;
+    sc.w = sc.zp + r * 32;
+    sc.x = sc.w + r * 32;
+    int* ibase = reinterpret_cast<int*>(base + 32 * (r * r + 5 * r)) + threadIdx.x;
+    sc.passive = ibase;
+    sc.idx = ibase + r * 32;
+    lh_column(AtA, Atb, btb, r, n, c, sc, H, status);
+}
+
+// Global-memory fallback for large r (one thread per column).
+__global__ void nnls_lh_kernel(const double* __restrict__ AtA, const double* __restrict__ Atb,
+                               const double* __restrict__ btb, int r, int n, double* __restrict__ H,
+                               double* __restrict__ scratch, int* __restrict__ iscratch, int* status)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    LhScratch sc;
+    sc.S = 1;
+    sc.L = scratch + (size_t)c * (r * r + 6 * r);
+    sc.y = sc.L + r * r;
+    sc.z = sc.y + r;
+    sc.zp = sc.z + r;
+    sc.w = sc.zp + r;
+    sc.x = sc.w + r;
+    sc.passive = iscratch + (size_t)c * 2 * r;
+    sc.idx = sc.passive + r;
+    lh_column(AtA, Atb, btb, r, n, c, sc, H, status);
+}
+
+size_t lh_smem_bytes(int r) { return 8ull * r * r + 32ull * (8ull * (r * r + 5 * r) + 4ull * 2 * r); }
 
 // ------------------------------------------------------------------- residual
 // Per-block partial sums of ||R - R(:,K)H||^2 and ||R||^2.
@@ -554,7 +617,17 @@ cudaError_t nnls_core(const double* R, int n, const int32_t* K, int r, double* H
     const int total = r * r + r * n + n;
     nnls_gram_kernel<<<(total + 127) / 128, 128, 0, s>>>(R, n, K, r, w.AtA, w.Atb, w.btb);
     count_launch();
-    nnls_lh_kernel<<<(n + 31) / 32, 32, 0, s>>>(w.AtA, w.Atb, w.btb, r, n, H, w.nnls, w.inls, status);
+    const size_t smem = lh_smem_bytes(r);
+    if (smem <= 200 * 1024) {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(nnls_lh_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        nnls_lh_smem_kernel<<<(n + 31) / 32, 32, smem, s>>>(w.AtA, w.Atb, w.btb, r, n, H, status);
+    } else {
+        nnls_lh_kernel<<<(n + 31) / 32, 32, 0, s>>>(w.AtA, w.Atb, w.btb, r, n, H, w.nnls, w.inls, status);
+    }
     count_launch();
     return cudaGetLastError();
 }
