@@ -178,6 +178,30 @@ mrnmf_status mrnmf_factorize_host(mrnmf_handle* handle, const float* X, int64_t 
                                   int32_t* K, double* H, double* resid, double* R, void* stream);
 
 /*
+ * The R / column-sum pass of mrnmf_tsqr_r (F32 input, FP32 form) for callers
+ * that cannot allocate device memory -- e.g. code running inside a host
+ * callback or an allocator hook, or under a memory pool the application owns
+ * outright.  The paper has no counterpart: this is a deployment variant.
+ * It needs no handle and allocates nothing (no cudaMalloc / cudaFree, no
+ * allocating library call): its scratch is a fixed 32 MiB __device__ array
+ * inside this library, held on every GPU that loads it until the process
+ * exits.  Limits: 1 <= n <= MRNMF_NMAX, m >= n, ldx >= n; m is unbounded
+ * (the pass uses fewer row streams when n is large so the scratch fits).
+ *   X      device, m-by-n row-major float32      R device n*n doubles out
+ *   colsum device n doubles out (nullable)
+ *   status device int32 out (nullable): 0, or the first device-side error
+ *          (MRNMF_ERR_BAD_INPUT), valid once the stream reaches it.
+ * Returns after enqueuing on `stream`; argument errors return at once.
+ * All calls share the one array per device: calls that overlap on the GPU
+ * race and give wrong results, so serialise them.  The array keeps the last
+ * call's contents; every call clears what must start at zero.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress),
+ * so make that first call before any stream capture.
+ */
+mrnmf_status mrnmf_tsqr_r_noalloc(const float* X, int64_t m, int32_t n, int64_t ldx, double* R, double* colsum,
+                                  int32_t* status, void* stream);
+
+/*
  * Instrumentation (no counterpart in the paper; used by benchmarks).
  * mrnmf_profile_events: when both are non-NULL, every later pass on this
  * handle records `ev_start` / `ev_stop` (cudaEvent_t created by the caller)

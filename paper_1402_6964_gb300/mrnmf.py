@@ -27,7 +27,7 @@ EXPORTS = [
     "mrnmf_create", "mrnmf_destroy", "mrnmf_last_error_string", "mrnmf_sync_status", "mrnmf_tsqr_r",
     "mrnmf_gauss_project", "mrnmf_tsqr_gp", "mrnmf_select_extreme", "mrnmf_nnls_h", "mrnmf_residual",
     "mrnmf_stream_begin", "mrnmf_stream_push", "mrnmf_stream_end", "mrnmf_factorize_host",
-    "mrnmf_profile_events", "mrnmf_kernel_launches",
+    "mrnmf_profile_events", "mrnmf_kernel_launches", "mrnmf_tsqr_r_noalloc",
 ]
 
 
@@ -69,6 +69,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mrnmf_factorize_host": ([P, P, i64, i32, i64, i32, i32, i32, i32, u64, P, P, P, P, P], st),
             "mrnmf_profile_events": ([P, P, P], st),
             "mrnmf_kernel_launches": ([], ctypes.c_uint64),
+            "mrnmf_tsqr_r_noalloc": ([P, i64, i32, i64, P, P, P, P], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -112,6 +113,16 @@ def _check_X(X):
 def kernel_launches() -> int:
     """Kernels launched by libmrnmf in this process so far."""
     return int(load().mrnmf_kernel_launches())
+
+
+def tsqr_r_noalloc(X, R, colsum=None, status=None, stream=None) -> int:
+    """mrnmf_tsqr_r_noalloc: R (and colsum) of a float32 CUDA X into caller
+    buffers, with no device allocation inside the library.  Returns the
+    C status of the call (device-side errors land in `status`)."""
+    _check_X(X)
+    m, n = X.shape
+    return int(load().mrnmf_tsqr_r_noalloc(_ptr(X), m, n, X.stride(0), _ptr(R), _ptr(colsum), _ptr(status),
+                                           _stream(stream)))
 
 
 class Handle:
