@@ -20,7 +20,9 @@ inline void count_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std
 struct PassState {
     int n = 0;
     int k = 0;          // Gaussian rows (0 = no projection)
-    int P = 0;          // number of streams (CTAs of the leaf kernel)
+    int P = 0;          // number of row streams (partial-sum slots)
+    int tri = 0;        // triangle slots the leaf leaves for the tree (P, or P / 4 when
+                        // the warp leaf folds each CTA's four streams into one)
     int fp64 = 0;       // 1: triangles and reflectors in binary64, else binary32
     int tc = 0;         // 1: tensor-core (TF32x3) leaf
     void* R = nullptr;      // P * n * n (dense row-major, zeros below diag), T = float or double

@@ -173,7 +173,9 @@ struct LhScratch {
 };
 
 // Solve AtA[idx,idx] z = rhs[idx] by Cholesky.  Returns false if the passive
-// block is not positive definite.
+// block is not positive definite.  The diagonal of L is stored inverted
+// (L[i][i] holds 1/l_ii): one binary64 reciprocal per pivot instead of a
+// division per entry -- binary64 division is a long sequence on GB300.
 __device__ bool chol_solve(const double* AtA, int r, const double* rhs, int S, const int* idx, int p, double* L,
                            double* y, double* z)
 {
@@ -183,21 +185,21 @@ __device__ bool chol_solve(const double* AtA, int r, const double* rhs, int S, c
             for (int q = 0; q < jj; ++q) s -= L[(i * p + q) * S] * L[(jj * p + q) * S];
             if (i == jj) {
                 if (!(s > 0.0)) return false;
-                L[(i * p + i) * S] = sqrt(s);
+                L[(i * p + i) * S] = 1.0 / sqrt(s);
             } else {
-                L[(i * p + jj) * S] = s / L[(jj * p + jj) * S];
+                L[(i * p + jj) * S] = s * L[(jj * p + jj) * S];
             }
         }
     }
     for (int i = 0; i < p; ++i) {
         double s = rhs[idx[i * S] * S];
         for (int q = 0; q < i; ++q) s -= L[(i * p + q) * S] * y[q * S];
-        y[i * S] = s / L[(i * p + i) * S];
+        y[i * S] = s * L[(i * p + i) * S];
     }
     for (int i = p - 1; i >= 0; --i) {
         double s = y[i * S];
         for (int q = i + 1; q < p; ++q) s -= L[(q * p + i) * S] * z[q * S];
-        z[i * S] = s / L[(i * p + i) * S];
+        z[i * S] = s * L[(i * p + i) * S];
     }
     return true;
 }
@@ -297,12 +299,13 @@ done:
     for (int i = 0; i < r; ++i) H[(size_t)i * n + c] = x[i * S];
 }
 
-// Shared-memory form: 32 columns per block, AtA staged in shared memory, each
-// thread's scratch interleaved with stride 32 (thread t owns element e at
-// [e * 32 + t]) so the 32 threads never hit the same bank.
+// Shared-memory form: C columns per block (one per thread of a warp, C <= 32),
+// AtA staged in shared memory, each thread's scratch interleaved with stride C
+// (thread t owns element e at [e * C + t]).  Few columns per block spread the
+// solves over many SMs: on GB300 each SM has few binary64 units.
 __global__ void __launch_bounds__(32) nnls_lh_smem_kernel(const double* __restrict__ AtA_g,
                                                           const double* __restrict__ Atb,
-                                                          const double* __restrict__ btb, int r, int n,
+                                                          const double* __restrict__ btb, int r, int n, int C,
                                                           double* __restrict__ H, int* status)
 {
     extern __shared__ __align__(16) double sm[];
@@ -310,20 +313,20 @@ __global__ void __launch_bounds__(32) nnls_lh_smem_kernel(const double* __restri
     double* base = sm + r * r;
     for (int i = threadIdx.x; i < r * r; i += 32) AtA[i] = AtA_g[i];
     __syncwarp();
-    const int c = blockIdx.x * 32 + threadIdx.x;
-    if (c >= n) return;
+    const int c = blockIdx.x * C + threadIdx.x;
+    if (threadIdx.x >= C || c >= n) return;
     LhScratch sc;
-    sc.S = 32;
+    sc.S = C;
     double* mine = base + threadIdx.x;
     sc.L = mine;
-    sc.y = sc.L + r * r * 32;
-    sc.z = sc.y + r * 32;
-    sc.zp = sc.z + r * 32;
-    sc.w = sc.zp + r * 32;
-    sc.x = sc.w + r * 32;
-    int* ibase = reinterpret_cast<int*>(base + 32 * (r * r + 5 * r)) + threadIdx.x;
+    sc.y = sc.L + r * r * C;
+    sc.z = sc.y + r * C;
+    sc.zp = sc.z + r * C;
+    sc.w = sc.zp + r * C;
+    sc.x = sc.w + r * C;
+    int* ibase = reinterpret_cast<int*>(base + C * (r * r + 5 * r)) + threadIdx.x;
     sc.passive = ibase;
-    sc.idx = ibase + r * 32;
+    sc.idx = ibase + r * C;
     lh_column(AtA, Atb, btb, r, n, c, sc, H, status);
 }
 
@@ -347,7 +350,7 @@ __global__ void nnls_lh_kernel(const double* __restrict__ AtA, const double* __r
     lh_column(AtA, Atb, btb, r, n, c, sc, H, status);
 }
 
-size_t lh_smem_bytes(int r) { return 8ull * r * r + 32ull * (8ull * (r * r + 5 * r) + 4ull * 2 * r); }
+size_t lh_smem_bytes(int r, int C) { return 8ull * r * r + (size_t)C * (8ull * (r * r + 5 * r) + 4ull * 2 * r); }
 
 // ------------------------------------------------------------------- residual
 // Per-block partial sums of ||R - R(:,K)H||^2 and ||R||^2.
@@ -617,14 +620,20 @@ cudaError_t nnls_core(const double* R, int n, const int32_t* K, int r, double* H
     const int total = r * r + r * n + n;
     nnls_gram_kernel<<<(total + 127) / 128, 128, 0, s>>>(R, n, K, r, w.AtA, w.Atb, w.btb);
     count_launch();
-    const size_t smem = lh_smem_bytes(r);
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int C = (n + sms - 1) / sms;  // columns per block: one block per SM when n <= #SMs
+    if (C > 32) C = 32;
+    while (C > 1 && lh_smem_bytes(r, C) > 200 * 1024) --C;
+    const size_t smem = lh_smem_bytes(r, C);
     if (smem <= 200 * 1024) {
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(nnls_lh_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);
             if (e != cudaSuccess) return e;
         }
-        nnls_lh_smem_kernel<<<(n + 31) / 32, 32, smem, s>>>(w.AtA, w.Atb, w.btb, r, n, H, status);
+        nnls_lh_smem_kernel<<<(n + C - 1) / C, 32, smem, s>>>(w.AtA, w.Atb, w.btb, r, n, C, H, status);
     } else {
         nnls_lh_kernel<<<(n + 31) / 32, 32, 0, s>>>(w.AtA, w.Atb, w.btb, r, n, H, w.nnls, w.inls, status);
     }

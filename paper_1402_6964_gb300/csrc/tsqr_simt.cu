@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "leaf.h"
 
 namespace mrnmf {
 
@@ -32,24 +33,6 @@ namespace {
 constexpr int kTileRows = 16;      // L: rows per tile and thread
 constexpr int kTriRows = 32;       // tile height in the tree
 constexpr int kFlushTiles = 64;    // binary32 partial sums flushed to binary64 every 64 tiles
-
-struct LeafArgs {
-    const void* X;
-    int64_t rows;          // rows of X in this launch
-    int64_t ldx;
-    int n;
-    int64_t rows_per_cta;  // leaf: rows per stream (multiple of L); tree: triangles per CTA
-    int64_t row_base;      // global row index of X's row 0 (Gaussian key)
-    const void* R_in;      // leaf: state to continue (nullptr = zeros); tree: input triangles
-    void* R_out;
-    int P_in;              // tree: number of input triangles
-    double* cs;            // P * n (+=), nullptr = skip
-    double* gx;            // P * k * n (+=), nullptr = skip
-    int k;
-    uint64_t seed;
-    int check;             // reject negative / NaN entries
-    int* status;
-};
 
 __host__ __device__ inline int packed_row(int j, int n) { return j * n - (j * (j + 1)) / 2; }
 
@@ -95,13 +78,16 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a)
     }
     const int64_t init_slot = TRI ? first_tri : cta;
     if (QR) {
-        for (int j = 0; j < n; ++j) {
-            if (own && c >= j) {
-                T v = T(0);
-                if (Rin && (!TRI || init_slot < a.P_in)) v = Rin[((size_t)init_slot * n + j) * n + c];
-                Rs[packed_row(j, n) + c] = v;
-            }
+        // independent loads over the whole triangle, unrolled so they overlap
+        const bool have = Rin && (!TRI || init_slot < a.P_in);
+        const T* src = have ? Rin + (size_t)init_slot * n * n : nullptr;
+        const int nn = n * n;
+#pragma unroll 8
+        for (int e = threadIdx.x; e < nn; e += nt) {
+            const int j = e / n, cc = e - j * n;
+            if (cc >= j) Rs[packed_row(j, n) + cc] = have ? src[e] : T(0);
         }
+        __syncthreads();
     }
 
     // ---- tile schedule ----
@@ -239,10 +225,13 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a)
     // ---- write the stream's triangle (dense, zeros below the diagonal) ----
     if (QR) {
         __syncthreads();
-        T* Rout = static_cast<T*>(a.R_out);
-        if (own)
-            for (int j = 0; j < n; ++j)
-                Rout[((size_t)cta * n + j) * n + c] = (c >= j) ? Rs[packed_row(j, n) + c] : T(0);
+        T* Rout = static_cast<T*>(a.R_out) + (size_t)cta * n * n;
+        const int nn = n * n;
+#pragma unroll 8
+        for (int e = threadIdx.x; e < nn; e += nt) {
+            const int j = e / n, cc = e - j * n;
+            Rout[e] = (cc >= j) ? Rs[packed_row(j, n) + cc] : T(0);
+        }
     }
 }
 
@@ -373,12 +362,22 @@ void pass_state_carve(PassState& st, void* base)
 int choose_streams(int n, int k, int fp64, int tc, int64_t m)
 {
     (void)tc;
-    // Enough resident CTAs to keep the SIMT pipes issuing while each stream
-    // waits at its per-column barrier, but no more: every extra stream adds a
-    // triangle to the tree.
+    if (!fp64 && warp_leaf_supported(n, k)) {
+        // one stream per warp; as many warps as the SM holds at once
+        const int w = warp_leaf_warps_per_cta();
+        int P = num_sms() * warp_leaf_ctas_per_sm(n, k) * w;
+        if (m > 0) {
+            const int64_t minrows = 2 * (int64_t)warp_leaf_rows_per_tile(n);
+            const int64_t cap = std::max<int64_t>(1, (m + minrows - 1) / minrows);
+            P = (int)std::min<int64_t>(P, cap);
+        }
+        return std::max(w, (P + w - 1) / w * w);
+    }
+    // CTA-per-stream kernel: enough resident CTAs to keep the SIMT pipes
+    // issuing while each stream waits at its per-column barrier, but no more:
+    // every extra stream adds a triangle to the tree.
     const int warps = (n + 31) / 32;
     int per_sm = fp64 ? 4 : std::max(2, std::min(8, 16 / warps));
-    (void)k;
     int P = num_sms() * per_sm;
     if (m > 0) {
         const int64_t minrows = 8 * kTileRows;
@@ -423,7 +422,16 @@ cudaError_t pass_push(PassState& st, const void* X, int64_t rows, int64_t ldx, i
     const int grid = st.P;  // every stream runs (possibly on zero rows) so its state slot is rewritten
     cudaError_t e;
     if (st.ev_leaf_start && (e = cudaEventRecord(st.ev_leaf_start, s)) != cudaSuccess) return e;
-    if (st.fp64) {
+    const bool warp_path = !st.fp64 && !xf64 && qr && warp_leaf_supported(st.n, st.k) &&
+                           st.P % warp_leaf_warps_per_cta() == 0;
+    st.tri = st.P;
+    if (warp_path) {
+        const int L = warp_leaf_rows_per_tile(st.n);
+        int64_t pw = (rows + st.P - 1) / st.P;
+        a.rows_per_cta = ((pw + L - 1) / L) * L;
+        e = launch_warp_leaf(a, st.P, s);
+        st.tri = st.P / warp_leaf_warps_per_cta();
+    } else if (st.fp64) {
         e = xf64 ? dispatch_leaf<double, double>(a, grid, qr, s) : dispatch_leaf<float, double>(a, grid, qr, s);
     } else {
         if (xf64) return cudaErrorInvalidValue;
@@ -439,8 +447,20 @@ static cudaError_t tree_and_finalize(PassState& st, double* R, int* status, cuda
 {
     const void* cur = st.R;
     void* bufs[2] = {st.Rtmp, st.R};
-    int Pc = st.P, which = 0;
+    int Pc = st.tri > 0 ? st.tri : st.P, which = 0;
     while (Pc > 1) {
+        if constexpr (is_f32<T>::value) {
+            if (wide_tree_supported(st.n)) {
+                int Pn = 0;
+                cudaError_t e = tree_wide_level(static_cast<const float*>(cur), Pc, st.n,
+                                                static_cast<float*>(bufs[which]), s, &Pn);
+                if (e != cudaSuccess) return e;
+                cur = bufs[which];
+                which ^= 1;
+                Pc = Pn;
+                continue;
+            }
+        }
         const int f = 2;
         const int Pn = (Pc + f - 1) / f;
         LeafArgs a{};

@@ -1,0 +1,586 @@
+// tsqr_warp.cu -- the pass over X for n <= 64 in binary32: one warp per row
+// stream (Sec. 3.5's map task), no block-wide barriers.
+//
+// Layout.  Lane l owns columns l and l+32 of the stream's tiles: the L rows of
+// those columns sit in its registers, so every reflector dot product is a
+// lane-local sum.  The stream's running triangle R (packed upper, binary32)
+// lives in the warp's slice of shared memory.  Tiles of L consecutive rows are
+// staged into shared memory by the TMA bulk-copy engine (cp.async.bulk with an
+// mbarrier) one tile ahead of the arithmetic, then moved to registers.
+//
+// Column step j on the stacked [R; A] (A = tile): the owner of column j
+// publishes the column's raw values in shared memory; every lane forms
+// g_c = A(:,j)' A(:,c) for its columns c >= j in one loop (g_j is the squared
+// norm sigma); then, with alpha = R_jj, beta = -sign(alpha) sqrt(alpha^2 +
+// sigma), s = 1/(alpha - beta), tau = (beta - alpha)/beta (the reflector
+// v = [e_j; s A(:,j)]), each column c > j gets w = R_jc + s g_c,
+// R_jc -= tau w, A(:,c) -= (tau w s) A(:,j) (evaluated with reciprocals of
+// beta and alpha - beta, since tau s = -1/beta).  The owner of column j+1 then
+// publishes its updated column.  One warp barrier per column, no block
+// barriers, no cross-lane reductions except the broadcast of sigma.
+//
+// Column sums and the Gaussian projection (Algorithm 1, with the combiner of
+// Sec. 3.2) are folded into the same pass: binary32 per tile, binary64 across
+// tiles.
+#include <cstdlib>
+
+#include "common.cuh"
+#include "internal.h"
+#include "leaf.h"
+
+namespace mrnmf {
+
+namespace {
+
+constexpr int kWarps = 4;  // streams per CTA
+constexpr int kFlush = 32;  // tiles between binary64 flushes of the partial sums
+
+// Tile heights: 128 rows when a lane owns one column (n <= 32), 32 rows when
+// it owns two (n <= 64): three 4-warp CTAs then fit per SM (measured faster
+// on GB300 than 64-row tiles with two CTAs; MRNMF_WARP_ROWS=64 selects those).
+
+__host__ __device__ inline int pk_row(int j, int n) { return j * n - (j * (j + 1)) / 2; }
+__host__ __device__ inline size_t up(size_t b, size_t a) { return (b + a - 1) / a * a; }
+
+// Per-warp shared-memory slice: [mbarrier | tile L*n | R packed | pub 2L | gbuf kp*L | gxs kp*n]
+template <int L>
+__host__ __device__ inline size_t warp_slice_bytes(int n, int k)
+{
+    const int kp = (k + 3) & ~3;
+    size_t b = 128;                                   // mbarrier (own 128 B so the tile is 128-aligned)
+    b += up(sizeof(float) * (size_t)L * n, 128);      // tile
+    b += up(sizeof(float) * (size_t)(n * (n + 1) / 2), 16);
+    b += sizeof(float) * 2 * L;                       // published column, double buffer
+    b += sizeof(float) * (size_t)kp * L;              // Gaussian tile, coordinate-major
+    b += sizeof(float) * (size_t)kp * n;              // projection accumulators
+    return up(b, 128);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the mbarrier phase `parity` to complete; false after ~1 s.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > 1000000000ull) return false;
+    }
+}
+
+// Householder column steps of the stacked [R; A] for one L-row tile A held in
+// registers (a0: column lane, a1: column lane + 32): R (packed, the warp's
+// shared memory) absorbs A; A is destroyed.  pub is the warp's 2L-float
+// publication buffer.
+template <int NC, int L>
+__device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2 ? L : 1], float* Rw, float* pub,
+                                             int n, int lane, bool own0, bool own1)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int c0 = lane, c1 = lane + 32;
+    if (lane == 0) {
+#pragma unroll
+        for (int l4 = 0; l4 < L / 4; ++l4)
+            reinterpret_cast<float4*>(pub)[l4] =
+                make_float4(a0[4 * l4], a0[4 * l4 + 1], a0[4 * l4 + 2], a0[4 * l4 + 3]);
+    }
+    __syncwarp();
+    for (int j = 0; j < n; ++j) {
+        const float4* pj = reinterpret_cast<const float4*>(pub + (j & 1) * L);
+        const bool act0 = j < 32;  // set 0 still holds columns >= j
+        float g0a = 0.f, g0b = 0.f, g0c = 0.f, g0d = 0.f, g1a = 0.f, g1b = 0.f, g1c = 0.f, g1d = 0.f;
+#pragma unroll
+        for (int l4 = 0; l4 < L / 4; ++l4) {
+            const float4 v = pj[l4];
+            if (act0) {
+                g0a = fmaf(v.x, a0[4 * l4], g0a);
+                g0b = fmaf(v.y, a0[4 * l4 + 1], g0b);
+                g0c = fmaf(v.z, a0[4 * l4 + 2], g0c);
+                g0d = fmaf(v.w, a0[4 * l4 + 3], g0d);
+            }
+            if (NC == 2) {
+                g1a = fmaf(v.x, a1[4 * l4], g1a);
+                g1b = fmaf(v.y, a1[4 * l4 + 1], g1b);
+                g1c = fmaf(v.z, a1[4 * l4 + 2], g1c);
+                g1d = fmaf(v.w, a1[4 * l4 + 3], g1d);
+            }
+        }
+        const float g0 = (g0a + g0b) + (g0c + g0d), g1 = (g1a + g1b) + (g1c + g1d);
+        const float sig = __shfl_sync(FULL, act0 ? g0 : g1, j & 31);
+        const int pr = pk_row(j, n);
+        const float alpha = Rw[pr + j];
+        __syncwarp();
+        // beta = -sign(alpha) sqrt(alpha^2 + sigma), d = alpha - beta.  With
+        // w' = d R_jc + g_c (= d w), the reflector's action is
+        // R_jc -= tau w  =  R_jc + w'/beta  and
+        // A(:,c) -= tau s w A(:,j)  =  A(:,c) + (w'/d)(1/beta) A(:,j).
+        // Reciprocals of beta and d (never of their product, which can
+        // underflow for a column already annihilated to rounding level).
+        float beta = alpha;
+        if (sig > 0.f) {
+            const float nrm = sqrtf(fmaf(alpha, alpha, sig));
+            beta = alpha >= 0.f ? -nrm : nrm;
+            const float d = alpha - beta;
+            const float rb = __frcp_rn(beta), rd = __frcp_rn(d);
+            float f0 = 0.f, f1 = 0.f;
+            if (act0 && own0 && c0 > j) {
+                const float r = Rw[pr + c0];
+                const float wp = fmaf(d, r, g0);
+                f0 = (wp * rd) * rb;
+                Rw[pr + c0] = fmaf(wp, rb, r);
+            }
+            if (NC == 2 && own1 && c1 > j) {
+                const float r = Rw[pr + c1];
+                const float wp = fmaf(d, r, g1);
+                f1 = (wp * rd) * rb;
+                Rw[pr + c1] = fmaf(wp, rb, r);
+            }
+#pragma unroll
+            for (int l4 = 0; l4 < L / 4; ++l4) {
+                const float4 v = pj[l4];
+                if (act0) {
+                    a0[4 * l4] = fmaf(f0, v.x, a0[4 * l4]);
+                    a0[4 * l4 + 1] = fmaf(f0, v.y, a0[4 * l4 + 1]);
+                    a0[4 * l4 + 2] = fmaf(f0, v.z, a0[4 * l4 + 2]);
+                    a0[4 * l4 + 3] = fmaf(f0, v.w, a0[4 * l4 + 3]);
+                }
+                if (NC == 2) {
+                    a1[4 * l4] = fmaf(f1, v.x, a1[4 * l4]);
+                    a1[4 * l4 + 1] = fmaf(f1, v.y, a1[4 * l4 + 1]);
+                    a1[4 * l4 + 2] = fmaf(f1, v.z, a1[4 * l4 + 2]);
+                    a1[4 * l4 + 3] = fmaf(f1, v.w, a1[4 * l4 + 3]);
+                }
+            }
+        }
+        if (lane == (j & 31)) Rw[pr + j] = beta;
+        // the owner of column j+1 publishes its updated values
+        const int jn = j + 1;
+        if (jn < n && lane == (jn & 31)) {
+            float4* dst = reinterpret_cast<float4*>(pub + (jn & 1) * L);
+            if (jn < 32) {
+#pragma unroll
+                for (int l4 = 0; l4 < L / 4; ++l4)
+                    dst[l4] = make_float4(a0[4 * l4], a0[4 * l4 + 1], a0[4 * l4 + 2], a0[4 * l4 + 3]);
+            } else if (NC == 2) {
+#pragma unroll
+                for (int l4 = 0; l4 < L / 4; ++l4)
+                    dst[l4] = make_float4(a1[4 * l4], a1[4 * l4 + 1], a1[4 * l4 + 2], a1[4 * l4 + 3]);
+            }
+        }
+        __syncwarp();
+    }
+
+}
+
+template <int NC, int L, bool GP>
+__global__ void __launch_bounds__(kWarps * 32) tsqr_warp_kernel(const LeafArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int n = a.n;
+    const int k = GP ? a.k : 0;
+    const int kp = (k + 3) & ~3;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ws = blockIdx.x * kWarps + warp;  // stream id = state slot
+    const unsigned FULL = 0xffffffffu;
+
+    unsigned char* base = smem + (size_t)warp * warp_slice_bytes<L>(n, k);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base);
+    float* tile = reinterpret_cast<float*>(base + 128);
+    float* Rw = reinterpret_cast<float*>(base + 128 + up(sizeof(float) * (size_t)L * n, 128));
+    float* pub = Rw + up((size_t)(n * (n + 1) / 2), 4);
+    float* gbuf = pub + 2 * L;
+    float* gxs = gbuf + (size_t)kp * L;
+
+    const int c0 = lane, c1 = lane + 32;
+    const bool own0 = c0 < n, own1 = NC == 2 && c1 < n;
+    const uint32_t bar_s = smem_u32(bar);
+
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // running triangle: warp 0 continues from the CTA's state slot (zeros on a
+    // fresh pass), the other warps start from zero -- the CTA's streams are
+    // folded into one triangle at the end of every launch
+    {
+        const float* Rin = static_cast<const float*>(a.R_in);
+        const int nn = n * n;
+        for (int e = lane; e < nn; e += 32) {
+            const int j = e / n, c = e - j * n;
+            if (c >= j) Rw[pk_row(j, n) + c] = (Rin && warp == 0) ? Rin[(size_t)blockIdx.x * nn + e] : 0.f;
+        }
+        for (int e = lane; e < kp * n; e += 32) gxs[e] = 0.f;
+    }
+    __syncwarp();
+
+    const int64_t r0 = (int64_t)ws * a.rows_per_cta;
+    const int64_t r1 = min(a.rows, r0 + a.rows_per_cta);
+    const int64_t ntiles = r1 > r0 ? (r1 - r0 + L - 1) / L : 0;
+    const float* X = static_cast<const float*>(a.X);
+    const bool tma_ok = a.ldx == n && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+
+    // Issue the TMA copy of tile t into `tile`; false if it must be loaded directly.
+    auto issue = [&](int64_t t) -> bool {
+        const int64_t row0 = r0 + t * L;
+        const int rows_v = (int)min((int64_t)L, r1 - row0);
+        const uint32_t bytes = (uint32_t)rows_v * (uint32_t)n * 4u;
+        if (!tma_ok || (bytes & 15u)) return false;
+        if (lane == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_s), "r"(bytes)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(tile)),
+                "l"(X + row0 * n), "r"(bytes), "r"(bar_s)
+                : "memory");
+        }
+        return true;
+    };
+
+    float a0[L], a1[NC == 2 ? L : 1];
+    float cs0 = 0.f, cs1 = 0.f;
+    bool bad = false;
+    uint32_t phase = 0;
+    bool inflight = ntiles > 0 ? issue(0) : false;
+
+    for (int64_t t = 0; t < ntiles; ++t) {
+        const int64_t row0 = r0 + t * L;
+        const int rows_v = (int)min((int64_t)L, r1 - row0);
+        if (inflight) {
+            // the decision is warp-uniform, so no lane leaves while others still shuffle
+            if (!__all_sync(FULL, mbar_wait(bar_s, phase))) {
+                if (lane == 0) set_status(a.status, MRNMF_ERR_TIMEOUT);
+                mbar_wait(bar_s, phase);  // bounded second wait for the copy in flight
+                break;                    // leave the tile loop; the CTA still meets at its barriers
+            }
+            phase ^= 1u;
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                a0[l] = (own0 && l < rows_v) ? tile[l * n + c0] : 0.f;
+                if (NC == 2) a1[l] = (own1 && l < rows_v) ? tile[l * n + c1] : 0.f;
+            }
+        } else {
+            const float* src = X + row0 * a.ldx;
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                a0[l] = (own0 && l < rows_v) ? src[(int64_t)l * a.ldx + c0] : 0.f;
+                if (NC == 2) a1[l] = (own1 && l < rows_v) ? src[(int64_t)l * a.ldx + c1] : 0.f;
+            }
+        }
+        __syncwarp();
+        if (t + 1 < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            inflight = issue(t + 1);
+        } else {
+            inflight = false;
+        }
+
+        // input check, column sums (Sec. 3.3)
+        {
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                bad |= !(a0[l] >= 0.f);
+                s0 += a0[l];
+                if (NC == 2) {
+                    bad |= !(a1[l] >= 0.f);
+                    s1 += a1[l];
+                }
+            }
+            cs0 += s0;
+            cs1 += s1;
+        }
+
+        if (GP) {
+            // G rows of this tile (coordinate-major), then GX(:, c) += G' A(:, c)
+            const int kq = kp >> 2;
+            for (int idx = lane; idx < L * kq; idx += 32) {
+                const int l = idx / kq, q = idx - l * kq;
+                float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (l < rows_v) g = gauss4(a.seed, a.row_base + row0 + l, (uint32_t)q);
+                gbuf[(4 * q + 0) * L + l] = g.x;
+                gbuf[(4 * q + 1) * L + l] = g.y;
+                gbuf[(4 * q + 2) * L + l] = g.z;
+                gbuf[(4 * q + 3) * L + l] = g.w;
+            }
+            __syncwarp();
+            for (int q = 0; q < k; ++q) {
+                const float4* gq = reinterpret_cast<const float4*>(gbuf + q * L);
+                float s0 = 0.f, s1 = 0.f, u0 = 0.f, u1 = 0.f;
+#pragma unroll
+                for (int l4 = 0; l4 < L / 4; ++l4) {
+                    const float4 g = gq[l4];
+                    s0 = fmaf(g.x, a0[4 * l4], s0);
+                    u0 = fmaf(g.y, a0[4 * l4 + 1], u0);
+                    s0 = fmaf(g.z, a0[4 * l4 + 2], s0);
+                    u0 = fmaf(g.w, a0[4 * l4 + 3], u0);
+                    if (NC == 2) {
+                        s1 = fmaf(g.x, a1[4 * l4], s1);
+                        u1 = fmaf(g.y, a1[4 * l4 + 1], u1);
+                        s1 = fmaf(g.z, a1[4 * l4 + 2], s1);
+                        u1 = fmaf(g.w, a1[4 * l4 + 3], u1);
+                    }
+                }
+                if (own0) gxs[q * n + c0] += s0 + u0;
+                if (NC == 2 && own1) gxs[q * n + c1] += s1 + u1;
+            }
+        }
+
+        column_steps<NC, L>(a0, a1, Rw, pub, n, lane, own0, own1);
+
+        if ((t + 1) % kFlush == 0 || t + 1 == ntiles) {
+            if (a.cs) {
+                if (own0) a.cs[(size_t)ws * n + c0] += (double)cs0;
+                if (own1) a.cs[(size_t)ws * n + c1] += (double)cs1;
+            }
+            cs0 = cs1 = 0.f;
+            if (GP && a.gx) {
+                for (int e = lane; e < k * n; e += 32) {
+                    a.gx[(size_t)ws * k * n + e] += (double)gxs[e];
+                    gxs[e] = 0.f;
+                }
+            }
+            __syncwarp();
+        }
+    }
+
+    if (a.check && __any_sync(FULL, bad)) {
+        if (lane == 0) set_status(a.status, MRNMF_ERR_BAD_INPUT);
+    }
+    // fold the CTA's four triangles into warp 0's: R([R0;R1;R2;R3]) by the
+    // same column steps, each absorbed triangle loaded as an L-row tile (L >= n)
+    for (int span = 1; span < kWarps; span <<= 1) {
+        __syncthreads();
+        if ((warp & (2 * span - 1)) == 0) {
+            const float* Rb = reinterpret_cast<const float*>(
+                smem + (size_t)(warp + span) * warp_slice_bytes<L>(n, k) + 128 + up(sizeof(float) * (size_t)L * n, 128));
+            for (int rb = 0; rb < n; rb += L) {  // the triangle's rows, L at a time
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    const int row = rb + l;
+                    a0[l] = (own0 && row < n && c0 >= row) ? Rb[pk_row(row, n) + c0] : 0.f;
+                    if (NC == 2) a1[l] = (own1 && row < n && c1 >= row) ? Rb[pk_row(row, n) + c1] : 0.f;
+                }
+                __syncwarp();
+                column_steps<NC, L>(a0, a1, Rw, pub, n, lane, own0, own1);
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float* Rout = static_cast<float*>(a.R_out) + (size_t)blockIdx.x * n * n;
+        const int nn = n * n;
+        for (int e = lane; e < nn; e += 32) {
+            const int j = e / n, c = e - j * n;
+            Rout[e] = (c >= j) ? Rw[pk_row(j, n) + c] : 0.f;
+        }
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Wide tree level for n <= 64: CTA q merges triangles [q*(S+1), (q+1)*(S+1)).
+// The first one seeds the running triangle (shared memory); thread (c, s)
+// holds column c of the s-th remaining triangle in registers (rows 0..c are
+// its only nonzeros, and reflectors 0..j-1 keep it that way).  Column step j:
+// sigma = sum over s of ||T_s(0..j, j)||^2 (two barriers per column: one after
+// the pivot columns and partial norms are published, one after the partial
+// dot products are), then every column c > j of every triangle is updated.
+template <int NP, int S>
+__global__ void __launch_bounds__(NP * S) tsqr_tree_wide_kernel(const float* __restrict__ Rin, int P_in, int n,
+                                                                float* __restrict__ Rout)
+{
+    __shared__ float Rs[NP * (NP + 1) / 2];
+    __shared__ __align__(16) float piv[2][S][NP];
+    __shared__ float sig[2][S];
+    __shared__ float dpart[2][S][NP];
+    const int c = threadIdx.x % NP, sgm = threadIdx.x / NP;
+    const int first = blockIdx.x * (S + 1);
+    const int tri = first + 1 + sgm;
+    const bool have = tri < P_in && c < n;
+    const int nn = n * n;
+    for (int e = threadIdx.x; e < nn; e += NP * S) {
+        const int j = e / n, cc = e - j * n;
+        if (cc >= j) Rs[pk_row(j, n) + cc] = first < P_in ? Rin[(size_t)first * nn + e] : 0.f;
+    }
+    float col[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) col[i] = (have && i <= c) ? Rin[(size_t)tri * nn + (size_t)i * n + c] : 0.f;
+    __syncthreads();
+
+    // Column c of every triangle is zero below row c, so the pivot column j has
+    // no entries past row j: every loop below stops at the first 4-row chunk
+    // past j and needs no masking.
+    for (int j = 0; j < n; ++j) {
+        const int b = j & 1;
+        float4* pv = reinterpret_cast<float4*>(&piv[b][sgm][0]);
+        if (c == j) {
+            float sg = 0.f;
+#pragma unroll
+            for (int q = 0; q < NP / 4; ++q) {
+                if (4 * q > j) break;
+                const float4 v = make_float4(col[4 * q], col[4 * q + 1], col[4 * q + 2], col[4 * q + 3]);
+                sg = fmaf(v.x, v.x, sg);
+                sg = fmaf(v.y, v.y, sg);
+                sg = fmaf(v.z, v.z, sg);
+                sg = fmaf(v.w, v.w, sg);
+                pv[q] = v;
+            }
+            sig[b][sgm] = sg;
+        }
+        __syncthreads();
+        float sigma = 0.f;
+#pragma unroll
+        for (int q = 0; q < S; ++q) sigma += sig[b][q];
+        const int pr = pk_row(j, n);
+        const float alpha = Rs[pr + j];
+        float beta = alpha, tau = 0.f, scale = 0.f;
+        if (sigma > 0.f) {
+            const float nrm = sqrtf(alpha * alpha + sigma);
+            beta = alpha >= 0.f ? -nrm : nrm;
+            scale = 1.f / (alpha - beta);
+            tau = (beta - alpha) / beta;
+        }
+        const bool upd = tau != 0.f && c > j && c < n;
+        const float r = upd ? Rs[pr + c] : 0.f;  // read before the barrier: segment 0 rewrites it after
+        if (upd) {
+            float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+            for (int q = 0; q < NP / 4; ++q) {
+                if (4 * q > j) break;
+                const float4 v = pv[q];
+                d0 = fmaf(v.x, col[4 * q], d0);
+                d1 = fmaf(v.y, col[4 * q + 1], d1);
+                d0 = fmaf(v.z, col[4 * q + 2], d0);
+                d1 = fmaf(v.w, col[4 * q + 3], d1);
+            }
+            dpart[b][sgm][c] = d0 + d1;
+        }
+        __syncthreads();
+        if (upd) {
+            float dsum = 0.f;
+#pragma unroll
+            for (int q = 0; q < S; ++q) dsum += dpart[b][q][c];
+            const float w = fmaf(scale, dsum, r);
+            const float f = tau * w * scale;
+#pragma unroll
+            for (int q = 0; q < NP / 4; ++q) {
+                if (4 * q > j) break;
+                const float4 v = pv[q];
+                col[4 * q] = fmaf(-f, v.x, col[4 * q]);
+                col[4 * q + 1] = fmaf(-f, v.y, col[4 * q + 1]);
+                col[4 * q + 2] = fmaf(-f, v.z, col[4 * q + 2]);
+                col[4 * q + 3] = fmaf(-f, v.w, col[4 * q + 3]);
+            }
+            if (sgm == 0) Rs[pr + c] = fmaf(-tau, w, r);
+        }
+        if (c == j && sgm == 0) Rs[pr + j] = beta;
+        // the next step writes the other buffers; this step's readers are past the barrier above
+    }
+    __syncthreads();
+    float* dst = Rout + (size_t)blockIdx.x * nn;
+    for (int e = threadIdx.x; e < nn; e += NP * S) {
+        const int j = e / n, cc = e - j * n;
+        dst[e] = cc >= j ? Rs[pk_row(j, n) + cc] : 0.f;
+    }
+}
+
+template <int NP, int S>
+cudaError_t launch_tree_wide(const float* Rin, int P_in, int n, float* Rout, cudaStream_t s, int* P_out)
+{
+    const int grid = (P_in + S) / (S + 1);
+    tsqr_tree_wide_kernel<NP, S><<<grid, NP * S, 0, s>>>(Rin, P_in, n, Rout);
+    count_launch();
+    *P_out = grid;
+    return cudaGetLastError();
+}
+
+template <int NC, int L, bool GP>
+cudaError_t launch_nc(const LeafArgs& a, int streams, cudaStream_t s)
+{
+    const size_t smem = (size_t)kWarps * warp_slice_bytes<L>(a.n, GP ? a.k : 0);
+    auto kern = tsqr_warp_kernel<NC, L, GP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (streams + kWarps - 1) / kWarps;
+    kern<<<grid, kWarps * 32, smem, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int NC, int L, bool GP>
+int ctas_per_sm_nc(int n, int k)
+{
+    const size_t smem = (size_t)kWarps * warp_slice_bytes<L>(n, GP ? k : 0);
+    auto kern = tsqr_warp_kernel<NC, L, GP>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kWarps * 32, smem) != cudaSuccess) return 1;
+    return blocks < 1 ? 1 : blocks;
+}
+
+// Tile height of the two-column form (32, or 64 when MRNMF_WARP_ROWS=64).
+int rows2()
+{
+    static int v = [] {
+        const char* e = getenv("MRNMF_WARP_ROWS");
+        return (e && atoi(e) == 64) ? 64 : 32;
+    }();
+    return v;
+}
+
+}  // namespace
+
+bool wide_tree_supported(int n) { return n >= 1 && n <= 64; }
+
+cudaError_t tree_wide_level(const float* Rin, int P_in, int n, float* Rout, cudaStream_t s, int* P_out)
+{
+    if (n <= 32) return launch_tree_wide<32, 16>(Rin, P_in, n, Rout, s, P_out);
+    return launch_tree_wide<64, 8>(Rin, P_in, n, Rout, s, P_out);
+}
+
+bool warp_leaf_supported(int n, int k)
+{
+    if (n < 1 || n > 64 || k > 64) return false;
+    const size_t smem = (size_t)kWarps * (n <= 32 ? warp_slice_bytes<128>(n, k)
+                                                  : (rows2() == 32 ? warp_slice_bytes<32>(n, k)
+                                                                   : warp_slice_bytes<64>(n, k)));
+    return smem <= 220 * 1024;
+}
+
+int warp_leaf_rows_per_tile(int n) { return n <= 32 ? 128 : rows2(); }
+
+int warp_leaf_warps_per_cta() { return kWarps; }
+
+int warp_leaf_ctas_per_sm(int n, int k)
+{
+    if (n <= 32) return k > 0 ? ctas_per_sm_nc<1, 128, true>(n, k) : ctas_per_sm_nc<1, 128, false>(n, k);
+    if (rows2() == 32) return k > 0 ? ctas_per_sm_nc<2, 32, true>(n, k) : ctas_per_sm_nc<2, 32, false>(n, k);
+    return k > 0 ? ctas_per_sm_nc<2, 64, true>(n, k) : ctas_per_sm_nc<2, 64, false>(n, k);
+}
+
+cudaError_t launch_warp_leaf(const LeafArgs& a, int streams, cudaStream_t s)
+{
+    const bool gp = a.gx != nullptr && a.k > 0;
+    if (a.n <= 32) return gp ? launch_nc<1, 128, true>(a, streams, s) : launch_nc<1, 128, false>(a, streams, s);
+    if (rows2() == 32) return gp ? launch_nc<2, 32, true>(a, streams, s) : launch_nc<2, 32, false>(a, streams, s);
+    return gp ? launch_nc<2, 64, true>(a, streams, s) : launch_nc<2, 64, false>(a, streams, s);
+}
+
+}  // namespace mrnmf
