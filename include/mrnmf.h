@@ -211,6 +211,20 @@ mrnmf_status mrnmf_tsqr_r_noalloc(const float* X, int64_t m, int32_t n, int64_t 
  * library has launched in the calling process so far.
  */
 mrnmf_status mrnmf_profile_events(mrnmf_handle* handle, void* ev_start, void* ev_stop);
+
+/*
+ * Diagnostics (no counterpart in the paper): one tcgen05 tensor-core GEMM
+ * D = A B^T on a single CTA, the datapath of the tensor-core forms.
+ *   A device 128-by-K float32 row-major, B device N-by-K float32 row-major,
+ *   D device 128-by-N float32 row-major out; 16 <= N <= 256, N % 16 == 0,
+ *   K in {32, 64}.
+ *   kind 0: TF32 inputs; 1: 3-pass split TF32 (hi*hi + hi*lo + lo*hi);
+ *   2: BF16 inputs.  FP32 accumulation in tensor memory.
+ *   status device int32 out (nullable): MRNMF_ERR_TIMEOUT if the MMA never
+ *   signalled completion within 1 s.
+ */
+mrnmf_status mrnmf_tc_selftest(const float* A, const float* B, float* D, int32_t N, int32_t K, int32_t kind,
+                               int32_t* status, void* stream);
 uint64_t mrnmf_kernel_launches(void);
 
 #ifdef __cplusplus

@@ -330,6 +330,198 @@ __global__ void __launch_bounds__(32) nnls_lh_smem_kernel(const double* __restri
     lh_column(AtA, Atb, btb, r, n, c, sc, H, status);
 }
 
+
+// ---------------------------------------------------------------------------
+// Lawson-Hanson with one warp per column (r <= 32): lane i holds coefficient i
+// (x_i, the dual w_i, passive flag) and, during a solve, row i of the
+// Cholesky factor of the passive block (Lrow) and its column (Lcol).  The
+// steps are the oracle's; every O(p) inner product runs across lanes, so each
+// Cholesky or triangular solve has O(p) latency instead of O(p^2).
+__device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+__global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restrict__ AtA_g,
+                                                           const double* __restrict__ Atb,
+                                                           const double* __restrict__ btb, int r, int n,
+                                                           double* __restrict__ H, int* status)
+{
+    __shared__ double AtA[32 * 32];
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) AtA[e] = AtA_g[e];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= n) return;
+    const unsigned FULL = 0xffffffffu;
+    const bool act = lane < r;
+    const double rhs = act ? Atb[(size_t)lane * n + c] : 0.0;
+    double maxdiag = act ? AtA[lane * r + lane] : 0.0;
+    for (int o = 16; o; o >>= 1) maxdiag = fmax(maxdiag, __shfl_xor_sync(FULL, maxdiag, o));
+    const double bb = btb[c];
+    const double tol = 1e-12 * sqrt(maxdiag * (bb > 0.0 ? bb : 0.0));
+    double x = 0.0;
+    bool passive = false;
+    int st = 0;
+    for (int outer = 0;; ++outer) {
+        // dual w = A^T b - A^T A x
+        double w = rhs;
+        for (int q = 0; q < r; ++q) {
+            const double xq = shfl_d(x, q);
+            if (act) w -= AtA[lane * r + q] * xq;
+        }
+        // entering index: the largest dual above tol among non-passive (lowest index on ties)
+        double best = (act && !passive && w > tol) ? w : -1.0;
+        int bi = lane;
+        for (int o = 16; o; o >>= 1) {
+            const double ob = __shfl_xor_sync(FULL, best, o);
+            const int oi = __shfl_xor_sync(FULL, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if (best <= 0.0) break;  // KKT satisfied (no dual above tol)
+        if (outer >= 3 * r) {
+            st = MRNMF_ERR_NOT_CONVERGED;
+            break;
+        }
+        if (lane == bi) passive = true;
+        for (int inner = 0; inner <= r + 1; ++inner) {
+            // passive indices in increasing order; lane k of the solve <-> idx[k]
+            const unsigned pm = __ballot_sync(FULL, act && passive);
+            const int p = __popc(pm);
+            const int my = act && passive ? __popc(pm & ((1u << lane) - 1u)) : -1;  // my rank, or -1
+            // lane k takes the k-th passive index
+            int idx = 0;
+            {
+                unsigned m = pm;
+                for (int k = 0; k < lane && m; ++k) m &= m - 1;
+                idx = m ? __ffs(m) - 1 : 0;
+            }
+            const bool in = lane < p;
+            double Lrow[32];
+            double Lcol[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                Lrow[q] = 0.0;
+                Lcol[q] = 0.0;
+            }
+            double invd = 0.0;  // 1 / L(k,k) for this lane's row k = lane
+            bool ok = true;
+            // right-looking Cholesky of AtA[idx, idx]
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                if (k >= p) break;
+                const int ik = __shfl_sync(FULL, idx, k);
+                double d = 0.0;
+                if (lane == k) {
+                    d = AtA[idx * r + idx];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        if (q < k) d -= Lrow[q] * Lrow[q];
+                }
+                d = shfl_d(d, k);
+                if (!(d > 0.0)) {
+                    ok = false;
+                    break;
+                }
+                const double ik_inv = 1.0 / sqrt(d);
+                if (lane == k) {
+                    Lrow[k] = 1.0 / ik_inv;
+                    invd = ik_inv;
+                }
+                // L(a,k) for a > k: (A(a,k) - sum_{q<k} L(a,q) L(k,q)) / L(k,k)
+                double s = (in && lane > k) ? AtA[idx * r + ik] : 0.0;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    if (q < k) {
+                        const double lkq = shfl_d(Lrow[q], k);
+                        s -= Lrow[q] * lkq;
+                    }
+                }
+                const double lak = (in && lane > k) ? s * ik_inv : 0.0;
+                if (in && lane > k) Lrow[k] = lak;
+                // lane k collects its column: L(a,k) for a > k
+#pragma unroll
+                for (int a = 0; a < 32; ++a) {
+                    if (a > k && a < p) {
+                        const double v = shfl_d(lak, a);
+                        if (lane == k) Lcol[a] = v;
+                    }
+                }
+            }
+            if (!__all_sync(FULL, ok)) {
+                st = MRNMF_ERR_RANK_DEFICIENT;
+                break;
+            }
+            // forward solve L y = rhs[idx]
+            const double bk = shfl_d(rhs, idx);  // lane k: rhs of its passive index (lanes >= p: junk, unused)
+            double acc = 0.0, y = 0.0;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                if (k >= p) break;
+                double yk = 0.0;
+                if (lane == k) {
+                    y = (bk - acc) * invd;
+                    yk = y;
+                }
+                yk = shfl_d(yk, k);
+                if (in && lane > k) acc += Lrow[k] * yk;
+            }
+            // backward solve L^T z = y: z_k = (y_k - sum_{a>k} L(a,k) z_a) / L(k,k)
+            double z = 0.0;
+            double acc2 = 0.0;
+#pragma unroll
+            for (int k = 31; k >= 0; --k) {
+                if (k >= p) continue;
+                double zk = 0.0;
+                if (lane == k) {
+                    z = (y - acc2) * invd;
+                    zk = z;
+                }
+                zk = shfl_d(zk, k);
+                // every lane a < k adds L(k,a) z_k: lane a holds L(k,a) in Lcol[k]
+                if (in && lane < k) acc2 += Lcol[k] * zk;
+            }
+            // scatter z back to coefficient lanes: coefficient i (passive, rank my) <- lane my's z
+            double zi = shfl_d(z, my < 0 ? 0 : my);
+            if (!(act && passive)) zi = 0.0;
+            const bool allpos = __all_sync(FULL, !(act && passive) || zi > 0.0);
+            if (allpos) {
+                x = zi;
+                break;
+            }
+            // step back to the feasible boundary
+            double a = 2.0;
+            int blk = 32;
+            if (act && passive && zi <= 0.0) {
+                const double den = x - zi;
+                a = den > 0.0 ? x / den : 0.0;
+                blk = lane;
+            }
+            for (int o = 16; o; o >>= 1) {
+                const double oa = __shfl_xor_sync(FULL, a, o);
+                const int ob = __shfl_xor_sync(FULL, blk, o);
+                if (oa < a || (oa == a && ob < blk)) {
+                    a = oa;
+                    blk = ob;
+                }
+            }
+            x += a * (zi - x);
+            if (lane == blk) x = 0.0;
+            if (act && passive && x <= 0.0) {
+                passive = false;
+                x = 0.0;
+            }
+            if (inner == r + 1) {
+                st = MRNMF_ERR_NOT_CONVERGED;
+                break;
+            }
+        }
+        if (st) break;
+    }
+    if (st && lane == 0) set_status(status, st);
+    if (act) H[(size_t)lane * n + c] = x;
+}
+
 // Global-memory fallback for large r (one thread per column).
 __global__ void nnls_lh_kernel(const double* __restrict__ AtA, const double* __restrict__ Atb,
                                const double* __restrict__ btb, int r, int n, double* __restrict__ H,
@@ -620,6 +812,11 @@ cudaError_t nnls_core(const double* R, int n, const int32_t* K, int r, double* H
     const int total = r * r + r * n + n;
     nnls_gram_kernel<<<(total + 127) / 128, 128, 0, s>>>(R, n, K, r, w.AtA, w.Atb, w.btb);
     count_launch();
+    if (r <= 32) {
+        nnls_lh_warp_kernel<<<(n + 3) / 4, 128, 0, s>>>(w.AtA, w.Atb, w.btb, r, n, H, status);
+        count_launch();
+        return cudaGetLastError();
+    }
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -309,8 +309,8 @@ __global__ void __launch_bounds__(kWarps * 32) tsqr_warp_kernel(const LeafArgs a
 
         if (GP) {
             // G rows of this tile (coordinate-major), then GX(:, c) += G' A(:, c)
-            const int kq = kp >> 2;
-            for (int idx = lane; idx < L * kq; idx += 32) {
+            const int kq = kp >> 2 > 0 ? kp >> 2 : 1;
+            for (int idx = lane; idx < L * (kp >> 2); idx += 32) {
                 const int l = idx / kq, q = idx - l * kq;
                 float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (l < rows_v) g = gauss4(a.seed, a.row_base + row0 + l, (uint32_t)q);

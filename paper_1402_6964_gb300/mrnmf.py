@@ -27,7 +27,7 @@ EXPORTS = [
     "mrnmf_create", "mrnmf_destroy", "mrnmf_last_error_string", "mrnmf_sync_status", "mrnmf_tsqr_r",
     "mrnmf_gauss_project", "mrnmf_tsqr_gp", "mrnmf_select_extreme", "mrnmf_nnls_h", "mrnmf_residual",
     "mrnmf_stream_begin", "mrnmf_stream_push", "mrnmf_stream_end", "mrnmf_factorize_host",
-    "mrnmf_profile_events", "mrnmf_kernel_launches", "mrnmf_tsqr_r_noalloc",
+    "mrnmf_profile_events", "mrnmf_kernel_launches", "mrnmf_tsqr_r_noalloc", "mrnmf_tc_selftest",
 ]
 
 
@@ -70,6 +70,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mrnmf_profile_events": ([P, P, P], st),
             "mrnmf_kernel_launches": ([], ctypes.c_uint64),
             "mrnmf_tsqr_r_noalloc": ([P, i64, i32, i64, P, P, P, P], st),
+            "mrnmf_tc_selftest": ([P, P, P, i32, i32, i32, P, P], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -123,6 +124,18 @@ def tsqr_r_noalloc(X, R, colsum=None, status=None, stream=None) -> int:
     m, n = X.shape
     return int(load().mrnmf_tsqr_r_noalloc(_ptr(X), m, n, X.stride(0), _ptr(R), _ptr(colsum), _ptr(status),
                                            _stream(stream)))
+
+
+def tc_selftest(A, B, kind="tf32x3", status=None, stream=None):
+    """D = A B^T on the tcgen05 tensor cores (A 128-by-K, B N-by-K, float32 CUDA)."""
+    import torch
+    N, K = B.shape
+    D = torch.empty((A.shape[0], N), dtype=torch.float32, device=A.device)
+    code = {"tf32": 0, "tf32x3": 1, "bf16": 2}[kind]
+    st = int(load().mrnmf_tc_selftest(_ptr(A), _ptr(B), _ptr(D), N, K, code, _ptr(status), _stream(stream)))
+    if st != OK:
+        raise MrnmfError(st, "tc_selftest rejected its arguments")
+    return D
 
 
 class Handle:
