@@ -137,6 +137,110 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_gp_pass(args):
+    """Projection-only pass (mrnmf_gauss_project): GB/s of X, tensor-core or SIMT."""
+    import torch
+
+    from paper_1402_6964_gb300 import build, mrnmf, synth
+
+    build.build()
+    w = synth.WORKLOADS[args.workload]
+    X, _ = synth.workload_matrix(w, m=args.rows)
+    Xd = torch.from_numpy(X).cuda()
+    h = mrnmf.Handle()
+    for _ in range(args.warmup):
+        h.gauss_project(Xd, w.k, w.seed)
+    h.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(args.steps):
+        h.gauss_project(Xd, w.k, w.seed)
+    b.record()
+    torch.cuda.synchronize()
+    h.sync()
+    ms = a.elapsed_time(b) / args.steps
+    hbm, _, src = _peaks()
+    gbs = 4.0 * X.shape[0] * X.shape[1] / ms / 1e6
+    print(json.dumps({"mode": "gp", "metric": "Gaussian projection pass GB/s of X", "value": gbs, "unit": "GB/s",
+                      "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+                      "path": "tcgen05 tf32x3" if os.environ.get("MRNMF_GP_TC") == "1" else "simt",
+                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                   "frac": gbs / hbm, "peak_source": src},
+                      "config": {"workload": w.name, "m": X.shape[0], "n": w.n, "k": w.k}}), flush=True)
+    h.close()
+
+
+def run_batched(args):
+    """256 independent problems (m log-uniform in [1e4, 1e7], n uniform in
+    10..128, r uniform in 3..min(16, n/2), sigma = 1e-3), drawn on the device:
+    rows/s of per-matrix mrnmf_tsqr_r calls, of one mrnmf_tsqr_r_batched call,
+    and of that call replayed as a CUDA graph."""
+    import torch
+
+    from paper_1402_6964_gb300 import build, mrnmf, synth
+
+    build.build()
+    torch.cuda.set_device(0)
+    specs = synth.batch_problems(args.batch, seed=1402005)
+    Xs = []
+    for i, (m, n, r) in enumerate(specs):
+        X, _ = synth.device_planted(m, n, r, seed=1402005 * 1000 + i, noise=1e-3)
+        Xs.append(X)
+    torch.cuda.synchronize()
+    rows = sum(m for m, _, _ in specs)
+    nbytes = sum(4.0 * m * n for m, n, _ in specs)
+    h = mrnmf.Handle()
+    outs = [(torch.empty((X.shape[1], X.shape[1]), dtype=torch.float64, device="cuda"),
+             torch.empty(X.shape[1], dtype=torch.float64, device="cuda")) for X in Xs]
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def per_matrix():
+        for X, (R, cs) in zip(Xs, outs):
+            h.tsqr_r(X, prec="fp32")
+
+    def batched():
+        h.tsqr_r_batched(Xs, outs=outs)
+
+    res = {}
+    for name, fn in (("per_matrix", per_matrix), ("batched", batched)):
+        for _ in range(args.warmup):
+            fn()
+        h.sync()
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(args.steps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        h.sync()
+        res[name] = a.elapsed_time(b) / args.steps
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            h.tsqr_r_batched(Xs, outs=outs, stream=st)
+    torch.cuda.current_stream().wait_stream(st)
+    for _ in range(args.warmup):
+        g.replay()
+    a, b = ev(), ev()
+    a.record()
+    for _ in range(args.steps):
+        g.replay()
+    b.record()
+    torch.cuda.synchronize()
+    h.sync()
+    res["batched_graph"] = a.elapsed_time(b) / args.steps
+    line = {"mode": "batched", "metric": "batched TSQR pass rows/s (and GB/s of X)", "unit": "rows/s",
+            "problems": len(specs), "rows": rows, "bytes": nbytes, "steps": args.steps, "warmup": args.warmup}
+    for k, ms in res.items():
+        line[k] = {"ms": ms, "rows_per_s": rows / ms * 1e3, "GBps": nbytes / ms / 1e6}
+    line["value"] = line["batched_graph"]["rows_per_s"]
+    print(json.dumps(line), flush=True)
+    h.close()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -290,6 +394,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["step", "gp", "batched"], default="step",
+                    help="step: the whole hot path (default); gp: the projection-only pass; "
+                         "batched: 256 independent problems")
+    ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--prec", choices=["auto", "fp32", "tf32x3"], default="auto")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--rows", type=int, default=None, help="first ROWS rows only (profiling a smaller case)")
@@ -302,6 +410,10 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "gp":
+        run_gp_pass(args)
+    elif args.mode == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -150,6 +150,21 @@ mrnmf_status mrnmf_residual(mrnmf_handle* handle, const double* R, int32_t n, co
                             const double* H, double* out, void* stream);
 
 /*
+ * Rank sweep (Sec. 2.2 and Sec. 2.4: with R in hand, the residual of many
+ * candidate separation ranks costs only n-by-n work; Sec. 5 picks r at an
+ * elbow of this curve).  Selects r_max columns once with `method` (SPA,
+ * greedy XRAY and GP all pick in a nested order, so the first r picks are the
+ * rank-r selection), then for r = 1..r_max solves H_r by NNLS on K[0..r) and
+ * writes curve[2(r-1)] = ||R - R(:,K_r) H_r||_F and
+ * curve[2(r-1)+1] = ||R - R(:,K_r) H_r||_F^2 / ||R||_F^2.
+ *   K     device r_max int32 out        curve device 2*r_max doubles out
+ * Other arguments as in mrnmf_select_extreme; 1 <= r_max <= min(n, 64).
+ */
+mrnmf_status mrnmf_rank_sweep(mrnmf_handle* handle, int32_t method, const double* R, int32_t n,
+                              const double* colsum, const double* GX, int32_t k, int32_t r_max, int32_t* K,
+                              double* curve, void* stream);
+
+/*
  * Streaming form of the pass (Sec. 3.4: one pass over data that arrives in
  * pieces).  begin() resets the handle's running state for n columns;
  * push() folds `rows` more rows into it (X_chunk device, row-major, ldx);
@@ -163,6 +178,35 @@ mrnmf_status mrnmf_stream_begin(mrnmf_handle* handle, int32_t n, int32_t dtype, 
 mrnmf_status mrnmf_stream_push(mrnmf_handle* handle, const void* X_chunk, int64_t rows, int64_t ldx,
                                void* stream);
 mrnmf_status mrnmf_stream_end(mrnmf_handle* handle, double* R, double* colsum, double* GX, void* stream);
+
+/*
+ * Batched pass: R (and colsum) of many independent problems of uneven m and n
+ * (Sec. 3.1's TSQR applied to each), FP32 form, enqueued on `stream` as a
+ * handful of launches for the whole batch: the row streams of all problems
+ * with n <= 64 share one leaf launch per tile shape, their trees one launch
+ * per level, and one launch writes every R and colsum; problems with n > 64
+ * run the one-problem pass in turn.  Each problem's share of the streams is
+ * planned on the host from its m and n (cost-balanced), tile height and tree
+ * fan-in follow n.
+ *   problems  host array of `count` descriptors (device X, R, colsum):
+ *             X float32 m-by-n row-major (ldx >= n), 1 <= n <= MRNMF_NMAX,
+ *             m >= n; R n*n doubles out; colsum n doubles out (nullable).
+ * Once a call has sized the handle's buffers, a repeat of the same batch
+ * issues no allocation or host synchronisation and can be captured in a CUDA
+ * graph; a captured graph keeps reading the handle's descriptor staging area,
+ * so make no batched call with a different batch on that handle while the
+ * graph is replayed.
+ */
+typedef struct {
+    const float* X;
+    int64_t m;
+    int64_t ldx;
+    int32_t n;
+    double* R;
+    double* colsum;
+} mrnmf_problem;
+
+mrnmf_status mrnmf_tsqr_r_batched(mrnmf_handle* handle, const mrnmf_problem* problems, int32_t count, void* stream);
 
 /*
  * End-to-end factorisation from HOST memory: streams X (host, row-major

@@ -12,32 +12,14 @@
 
 #include "../../include/mrnmf.h"
 #include "internal.h"
+#include "handle.h"
+#include "leaf.h"
 
-struct mrnmf_handle {
-    int device = -1;
-    int* d_status = nullptr;
-    void* ws = nullptr;  // pass state
-    size_t ws_bytes = 0;
-    void* sws = nullptr;  // small-step workspace
-    size_t sws_bytes = 0;
-    std::string err = "no error";
-    // streaming
-    bool open = false;
-    int xdtype = MRNMF_F32;
-    mrnmf::PassState st;
-    // host end-to-end path
-    void* xbuf = nullptr;
-    size_t xbuf_bytes = 0;
-    double* dout = nullptr;
-    size_t dout_bytes = 0;
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
-    cudaEvent_t ev_done[2] = {nullptr, nullptr};
-    // instrumentation
-    cudaEvent_t prof_start = nullptr, prof_stop = nullptr;
-};
 
-namespace {
+
+
+namespace mrnmf {
+namespace api {
 
 mrnmf_status fail(mrnmf_handle* h, mrnmf_status s, const std::string& msg)
 {
@@ -148,7 +130,10 @@ mrnmf_status run_pass(mrnmf_handle* h, const void* X, int64_t m, int32_t n, int6
     return MRNMF_OK;
 }
 
-}  // namespace
+}  // namespace api
+}  // namespace mrnmf
+
+using namespace mrnmf::api;
 
 extern "C" {
 
@@ -172,6 +157,10 @@ void mrnmf_destroy(mrnmf_handle* h)
         cudaFree(h->sws);
         cudaFree(h->xbuf);
         cudaFree(h->dout);
+        cudaFree(h->sweep);
+        cudaFree(h->bws);
+        if (h->bstage) cudaFreeHost(h->bstage);
+        if (h->ev_bstage) cudaEventDestroy(h->ev_bstage);
         for (int i = 0; i < 2; ++i) {
             if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
             if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
@@ -305,6 +294,24 @@ mrnmf_status mrnmf_residual(mrnmf_handle* h, const double* R, int32_t n, const i
         return s;
     cudaError_t e = mrnmf::residual(R, n, K, r, H, out, h->sws, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(h, e, "residual");
+    return MRNMF_OK;
+}
+
+mrnmf_status mrnmf_rank_sweep(mrnmf_handle* h, int32_t method, const double* R, int32_t n, const double* colsum,
+                              const double* GX, int32_t k, int32_t r_max, int32_t* K, double* curve, void* stream)
+{
+    if (!h) return MRNMF_ERR_INVALID_ARG;
+    if (!R || !K || !curve) return fail(h, MRNMF_ERR_INVALID_ARG, "R, K and curve are required");
+    if (n < 1 || n > MRNMF_NMAX || r_max < 1 || r_max > n || r_max > 64)
+        return fail(h, MRNMF_ERR_INVALID_ARG, "need 1 <= r_max <= min(n, 64), n <= 256");
+    mrnmf_status s = mrnmf_select_extreme(h, method, R, n, colsum, GX, k, r_max, K, nullptr, stream);
+    if (s != MRNMF_OK) return s;
+    if ((s = grow(h, &h->sweep, &h->sweep_bytes, 8ull * r_max * n, "rank sweep scratch")) != MRNMF_OK) return s;
+    double* H = static_cast<double*>(h->sweep);
+    for (int r = 1; r <= r_max; ++r) {
+        if ((s = mrnmf_nnls_h(h, R, n, K, r, H, stream)) != MRNMF_OK) return s;
+        if ((s = mrnmf_residual(h, R, n, K, r, H, curve + 2 * (r - 1), stream)) != MRNMF_OK) return s;
+    }
     return MRNMF_OK;
 }
 

@@ -70,4 +70,9 @@ cudaError_t residual(const double* R, int n, const int32_t* K, int r, const doub
 // ---- tensor-core leaf (tsqr_tc.cu) ----
 bool tc_supported(int n);
 
+// ---- tensor-core Gaussian projection pass (gp_tc.cu) ----
+bool gp_tc_supported(int n, int k);
+cudaError_t launch_gp_tc(const float* X, int64_t rows, int64_t ldx, int n, int k, int64_t row_base, uint64_t seed,
+                         int max_ctas, double* cs, double* gx, int* status, cudaStream_t s);
+
 }  // namespace mrnmf

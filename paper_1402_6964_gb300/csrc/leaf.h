@@ -25,12 +25,40 @@ struct LeafArgs {
     int* status;
 };
 
+// Batched pass: one problem per entry, CTAs described one by one.
+struct BatchProblem {
+    const float* X;
+    int64_t m;
+    int64_t ldx;
+    int n;
+    int64_t rows_per_stream;  // multiple of the family's tile height
+    float* tri;               // this problem's leaf triangles (one per CTA, n*n each)
+    double* cs;               // this problem's partial column sums (one n-vector per stream)
+};
+struct BatchCta {
+    int p;    // problem
+    int cta;  // CTA index within the problem (streams 4*cta .. 4*cta+3)
+};
+
+struct TreeCta {
+    const float* in;  // `count` consecutive n*n triangles
+    int count;        // 1 .. fan-in
+    int n;
+    float* out;       // one n*n triangle
+};
+
 // Warp-per-stream leaf (tsqr_warp.cu): binary32, n <= 64.  Streams = grid * warps_per_cta().
 bool warp_leaf_supported(int n, int k);
 int warp_leaf_rows_per_tile(int n);
 int warp_leaf_warps_per_cta();
 int warp_leaf_ctas_per_sm(int n, int k);
 cudaError_t launch_warp_leaf(const LeafArgs& a, int streams, cudaStream_t s);
+// family 1: n <= 32 (128-row tiles), family 2: 33 <= n <= 64 (32-row tiles)
+cudaError_t launch_warp_batched(const BatchCta* desc, int nctas, const BatchProblem* probs, int family, int max_n,
+                                int* status, cudaStream_t s);
+int warp_batched_rows_per_tile(int family);
+int tree_fan_in(int family);  // triangles folded per tree CTA
+cudaError_t launch_tree_batched(const TreeCta* desc, int nctas, int family, cudaStream_t s);
 
 // Wide tree level (binary32, n <= 64): P_in triangles -> *P_out = ceil(P_in / (S+1)).
 bool wide_tree_supported(int n);

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "internal.h"
@@ -425,7 +426,19 @@ cudaError_t pass_push(PassState& st, const void* X, int64_t rows, int64_t ldx, i
     const bool warp_path = !st.fp64 && !xf64 && qr && warp_leaf_supported(st.n, st.k) &&
                            st.P % warp_leaf_warps_per_cta() == 0;
     st.tri = st.P;
-    if (warp_path) {
+    // The projection-only pass runs on SIMT cores by default: G's generation
+    // (Philox + Box-Muller), not the k-by-n product, dominates it, and the
+    // tcgen05 form measured slower on GB300 (525 vs 727 GB/s at 1e7 x 50, k = 20).
+    // MRNMF_GP_TC=1 selects the tcgen05 (3-pass TF32) form.
+    static const bool gp_tc = [] {
+        const char* v = getenv("MRNMF_GP_TC");
+        return v && v[0] == '1';
+    }();
+    if (!qr && !st.fp64 && !xf64 && st.k > 0 && gp_tc && gp_tc_supported(st.n, st.k)) {
+        // projection-only pass on the tensor cores
+        e = launch_gp_tc(static_cast<const float*>(X), rows, ldx, st.n, st.k, st.rows_seen, st.seed, st.P, st.cs,
+                         st.gx, status, s);
+    } else if (warp_path) {
         const int L = warp_leaf_rows_per_tile(st.n);
         int64_t pw = (rows + st.P - 1) / st.P;
         a.rows_per_cta = ((pw + L - 1) / L) * L;

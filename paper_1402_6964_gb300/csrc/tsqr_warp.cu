@@ -189,14 +189,14 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
 }
 
 template <int NC, int L, bool GP>
-__global__ void __launch_bounds__(kWarps * 32) tsqr_warp_kernel(const LeafArgs a)
+__device__ __forceinline__ void warp_stream_body(const LeafArgs& a, const int cta)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int n = a.n;
     const int k = GP ? a.k : 0;
     const int kp = (k + 3) & ~3;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ws = blockIdx.x * kWarps + warp;  // stream id = state slot
+    const int ws = cta * kWarps + warp;  // stream id within the problem = partial-sum slot
     const unsigned FULL = 0xffffffffu;
 
     unsigned char* base = smem + (size_t)warp * warp_slice_bytes<L>(n, k);
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kWarps * 32) tsqr_warp_kernel(const LeafArgs a
         const int nn = n * n;
         for (int e = lane; e < nn; e += 32) {
             const int j = e / n, c = e - j * n;
-            if (c >= j) Rw[pk_row(j, n) + c] = (Rin && warp == 0) ? Rin[(size_t)blockIdx.x * nn + e] : 0.f;
+            if (c >= j) Rw[pk_row(j, n) + c] = (Rin && warp == 0) ? Rin[(size_t)cta * nn + e] : 0.f;
         }
         for (int e = lane; e < kp * n; e += 32) gxs[e] = 0.f;
     }
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(kWarps * 32) tsqr_warp_kernel(const LeafArgs a
     }
     __syncthreads();
     if (warp == 0) {
-        float* Rout = static_cast<float*>(a.R_out) + (size_t)blockIdx.x * n * n;
+        float* Rout = static_cast<float*>(a.R_out) + (size_t)cta * n * n;
         const int nn = n * n;
         for (int e = lane; e < nn; e += 32) {
             const int j = e / n, c = e - j * n;
@@ -393,6 +393,34 @@ __global__ void __launch_bounds__(kWarps * 32) tsqr_warp_kernel(const LeafArgs a
     }
 }
 
+
+template <int NC, int L, bool GP>
+__global__ void __launch_bounds__(kWarps * 32) tsqr_warp_kernel(const LeafArgs a)
+{
+    warp_stream_body<NC, L, GP>(a, blockIdx.x);
+}
+
+// Batched form: CTA b works on problem desc[b].p, as that problem's CTA desc[b].cta.
+template <int NC, int L>
+__global__ void __launch_bounds__(kWarps * 32) tsqr_warp_batched_kernel(const BatchCta* __restrict__ desc,
+                                                                        const BatchProblem* __restrict__ probs,
+                                                                        int* status)
+{
+    const BatchCta d = desc[blockIdx.x];
+    const BatchProblem pb = probs[d.p];
+    LeafArgs a{};
+    a.X = pb.X;
+    a.rows = pb.m;
+    a.ldx = pb.ldx;
+    a.n = pb.n;
+    a.rows_per_cta = pb.rows_per_stream;
+    a.R_in = nullptr;
+    a.R_out = pb.tri;
+    a.cs = pb.cs;
+    a.check = 1;
+    a.status = status;
+    warp_stream_body<NC, L, false>(a, d.cta);
+}
 
 // ---------------------------------------------------------------------------
 // Wide tree level for n <= 64: CTA q merges triangles [q*(S+1), (q+1)*(S+1)).
@@ -403,15 +431,14 @@ __global__ void __launch_bounds__(kWarps * 32) tsqr_warp_kernel(const LeafArgs a
 // the pivot columns and partial norms are published, one after the partial
 // dot products are), then every column c > j of every triangle is updated.
 template <int NP, int S>
-__global__ void __launch_bounds__(NP * S) tsqr_tree_wide_kernel(const float* __restrict__ Rin, int P_in, int n,
-                                                                float* __restrict__ Rout)
+__device__ __forceinline__ void tree_wide_body(const float* __restrict__ Rin, int first, int P_in, int n,
+                                               float* __restrict__ dst)
 {
     __shared__ float Rs[NP * (NP + 1) / 2];
     __shared__ __align__(16) float piv[2][S][NP];
     __shared__ float sig[2][S];
     __shared__ float dpart[2][S][NP];
     const int c = threadIdx.x % NP, sgm = threadIdx.x / NP;
-    const int first = blockIdx.x * (S + 1);
     const int tri = first + 1 + sgm;
     const bool have = tri < P_in && c < n;
     const int nn = n * n;
@@ -494,11 +521,25 @@ __global__ void __launch_bounds__(NP * S) tsqr_tree_wide_kernel(const float* __r
         // the next step writes the other buffers; this step's readers are past the barrier above
     }
     __syncthreads();
-    float* dst = Rout + (size_t)blockIdx.x * nn;
     for (int e = threadIdx.x; e < nn; e += NP * S) {
         const int j = e / n, cc = e - j * n;
         dst[e] = cc >= j ? Rs[pk_row(j, n) + cc] : 0.f;
     }
+}
+
+template <int NP, int S>
+__global__ void __launch_bounds__(NP * S) tsqr_tree_wide_kernel(const float* __restrict__ Rin, int P_in, int n,
+                                                                float* __restrict__ Rout)
+{
+    tree_wide_body<NP, S>(Rin, blockIdx.x * (S + 1), P_in, n, Rout + (size_t)blockIdx.x * n * n);
+}
+
+// Batched tree level: CTA b folds desc[b].count triangles at desc[b].in into desc[b].out.
+template <int NP, int S>
+__global__ void __launch_bounds__(NP * S) tsqr_tree_wide_batched_kernel(const TreeCta* __restrict__ desc)
+{
+    const TreeCta d = desc[blockIdx.x];
+    tree_wide_body<NP, S>(d.in, 0, d.count, d.n, d.out);
 }
 
 template <int NP, int S>
@@ -573,6 +614,42 @@ int warp_leaf_ctas_per_sm(int n, int k)
     if (n <= 32) return k > 0 ? ctas_per_sm_nc<1, 128, true>(n, k) : ctas_per_sm_nc<1, 128, false>(n, k);
     if (rows2() == 32) return k > 0 ? ctas_per_sm_nc<2, 32, true>(n, k) : ctas_per_sm_nc<2, 32, false>(n, k);
     return k > 0 ? ctas_per_sm_nc<2, 64, true>(n, k) : ctas_per_sm_nc<2, 64, false>(n, k);
+}
+
+cudaError_t launch_warp_batched(const BatchCta* desc, int nctas, const BatchProblem* probs, int family, int max_n,
+                                int* status, cudaStream_t s)
+{
+    if (nctas <= 0) return cudaSuccess;
+    cudaError_t e;
+    size_t smem;
+    if (family == 1) {
+        smem = (size_t)kWarps * warp_slice_bytes<128>(max_n, 0);
+        e = cudaFuncSetAttribute(tsqr_warp_batched_kernel<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        tsqr_warp_batched_kernel<1, 128><<<nctas, kWarps * 32, smem, s>>>(desc, probs, status);
+    } else {
+        smem = (size_t)kWarps * warp_slice_bytes<32>(max_n, 0);
+        e = cudaFuncSetAttribute(tsqr_warp_batched_kernel<2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        tsqr_warp_batched_kernel<2, 32><<<nctas, kWarps * 32, smem, s>>>(desc, probs, status);
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+int warp_batched_rows_per_tile(int family) { return family == 1 ? 128 : 32; }
+
+int tree_fan_in(int family) { return family == 1 ? 17 : 9; }
+
+cudaError_t launch_tree_batched(const TreeCta* desc, int nctas, int family, cudaStream_t s)
+{
+    if (nctas <= 0) return cudaSuccess;
+    if (family == 1) tsqr_tree_wide_batched_kernel<32, 16><<<nctas, 32 * 16, 0, s>>>(desc);
+    else tsqr_tree_wide_batched_kernel<64, 8><<<nctas, 64 * 8, 0, s>>>(desc);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_warp_leaf(const LeafArgs& a, int streams, cudaStream_t s)

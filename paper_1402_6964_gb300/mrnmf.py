@@ -28,7 +28,14 @@ EXPORTS = [
     "mrnmf_gauss_project", "mrnmf_tsqr_gp", "mrnmf_select_extreme", "mrnmf_nnls_h", "mrnmf_residual",
     "mrnmf_stream_begin", "mrnmf_stream_push", "mrnmf_stream_end", "mrnmf_factorize_host",
     "mrnmf_profile_events", "mrnmf_kernel_launches", "mrnmf_tsqr_r_noalloc", "mrnmf_tc_selftest",
+    "mrnmf_rank_sweep", "mrnmf_tsqr_r_batched",
 ]
+
+
+class Problem(ctypes.Structure):
+    """mrnmf_problem: one member of a batched pass."""
+    _fields_ = [("X", ctypes.c_void_p), ("m", ctypes.c_int64), ("ldx", ctypes.c_int64), ("n", ctypes.c_int32),
+                ("R", ctypes.c_void_p), ("colsum", ctypes.c_void_p)]
 
 
 class MrnmfError(RuntimeError):
@@ -71,6 +78,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mrnmf_kernel_launches": ([], ctypes.c_uint64),
             "mrnmf_tsqr_r_noalloc": ([P, i64, i32, i64, P, P, P, P], st),
             "mrnmf_tc_selftest": ([P, P, P, i32, i32, i32, P, P], st),
+            "mrnmf_rank_sweep": ([P, i32, P, i32, P, P, i32, i32, P, P, P], st),
+            "mrnmf_tsqr_r_batched": ([P, P, i32, P], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -248,6 +257,37 @@ class Handle:
         self.check(self._lib.mrnmf_residual(self.h, _ptr(R), n, _ptr(K), K.shape[0], _ptr(H), _ptr(o),
                                             _stream(stream)))
         return o
+
+    def rank_sweep(self, method, R=None, colsum=None, GX=None, r_max=1, stream=None):
+        """(K for r_max, curve[r-1] = (abs, rel) residual for r = 1..r_max)."""
+        import torch
+        ref = R if R is not None else GX
+        n = ref.shape[1]
+        k = GX.shape[0] if GX is not None else 0
+        K = torch.empty(r_max, dtype=torch.int32, device=ref.device)
+        curve = torch.empty((r_max, 2), dtype=torch.float64, device=ref.device)
+        self.check(self._lib.mrnmf_rank_sweep(self.h, METHOD[method], _ptr(R), n, _ptr(colsum), _ptr(GX), k, r_max,
+                                              _ptr(K), _ptr(curve), _stream(stream)))
+        return K, curve
+
+    def tsqr_r_batched(self, Xs, outs=None, stream=None):
+        """R and colsum of every float32 CUDA matrix in Xs, one batched pass.
+        outs: optional list of (R, colsum) tensors to fill (reused across calls)."""
+        import torch
+        if outs is None:
+            outs = [(torch.empty((X.shape[1], X.shape[1]), dtype=torch.float64, device=X.device),
+                     torch.empty(X.shape[1], dtype=torch.float64, device=X.device)) for X in Xs]
+        arr = (Problem * len(Xs))()
+        for i, (X, (R, cs)) in enumerate(zip(Xs, outs)):
+            _check_X(X)
+            if X.dtype != torch.float32:
+                raise TypeError("batched pass takes float32")
+            arr[i] = Problem(X.data_ptr(), X.shape[0], X.stride(0), X.shape[1], R.data_ptr(),
+                             cs.data_ptr() if cs is not None else None)
+        self._batch = arr  # keep the descriptors alive
+        self.check(self._lib.mrnmf_tsqr_r_batched(self.h, ctypes.cast(arr, ctypes.c_void_p), len(Xs),
+                                                  _stream(stream)))
+        return outs
 
     # ------------------------------------------------------------ streaming
     def stream_begin(self, n, dtype="f32", prec="auto", k=0, seed=0, stream=None):

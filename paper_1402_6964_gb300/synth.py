@@ -143,3 +143,20 @@ def random_nonneg(m: int, n: int, seed: int, dtype=np.float32, integer: bool = F
     if integer:
         return g.integers(0, 8, size=(m, n)).astype(dtype)
     return g.random((m, n)).astype(dtype)
+
+
+def device_planted(m: int, n: int, r: int, seed: int, noise: float = 0.0, alpha: float = 1.0, device="cuda"):
+    """The planted separable X of `planted_separable` drawn on the GPU with
+    torch's counter-based generator (same recipe, different stream of random
+    numbers): for workloads too large to draw on the host.  float32."""
+    import torch
+    P = planted_structure(n, r, seed, alpha)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) * 1000003 + 11)
+    W = torch.rand((m, r), generator=g, device=device, dtype=torch.float32)
+    X = W @ torch.from_numpy(P.Hmix.astype(np.float32)).to(device)
+    del W
+    if noise > 0:
+        X.add_(torch.randn((m, n), generator=g, device=device, dtype=torch.float32), alpha=noise)
+        X.clamp_(min=0.0)
+    return X, P

@@ -337,3 +337,31 @@ def test_full_size_near_separable(h, oracle):
     Ko, go = oracle.spa(Rc, X64.sum(0), w.r)
     compare_K(host(K), Ko, go, k_margin(Rg, Rc))
     assert sorted(host(K)) == list(P.K)
+
+
+@pytest.mark.parametrize("method", ["spa", "xray", "gp"])
+def test_rank_sweep(h, oracle, reduced, method):
+    # Sec. 2.4 / Sec. 5: residual for every r <= r_max from one R, against the
+    # oracle's NNLS + residual on the oracle's nested picks (same inputs)
+    X, P, Ro, so, GXo = reduced
+    r_max = 12
+    if method == "gp":  # GP only ever proposes extreme points: sweep up to its candidate count
+        r_max = min(r_max, len(oracle.gp_select(GXo, so, 1)[1]))
+    K, curve = h.rank_sweep(method, R=dev(Ro), colsum=dev(so), GX=dev(GXo) if method == "gp" else None, r_max=r_max)
+    h.sync()
+    if method == "spa":
+        Ko, _ = oracle.spa(Ro, so, r_max)
+    elif method == "xray":
+        Ko, _, _ = oracle.xray(Ro, r_max)
+    else:
+        Ko, _, _ = oracle.gp_select(GXo, so, r_max)
+    assert list(host(K)) == list(Ko)
+    cv = host(curve)
+    for r in range(1, r_max + 1):
+        Hr, _ = oracle.nnls_h(Ro, Ko[:r])
+        ab, rel = oracle.residual(Ro, Ko[:r], Hr)
+        assert cv[r - 1, 0] == pytest.approx(ab, rel=1e-8, abs=1e-12)
+        assert cv[r - 1, 1] == pytest.approx(rel, rel=1e-8, abs=1e-20)
+    # the curve drops to the noise floor at the planted rank (9) for SPA and GP
+    if method != "xray" and r_max >= 9:
+        assert cv[8, 1] < 1e-4 * cv[0, 1]
