@@ -57,6 +57,12 @@ cudaError_t launch_warp_leaf(const LeafArgs& a, int streams, cudaStream_t s);
 cudaError_t launch_warp_batched(const BatchCta* desc, int nctas, const BatchProblem* probs, int family, int max_n,
                                 int* status, cudaStream_t s);
 int warp_batched_rows_per_tile(int family);
+
+// CTA-per-stream leaf (tsqr_warp.cu): binary32, 64 < n <= 256.
+bool cta_leaf_supported(int n, int k);
+int cta_leaf_rows_per_tile();
+int cta_leaf_ctas_per_sm(int n, int k);
+cudaError_t launch_cta_leaf(const LeafArgs& a, int grid, cudaStream_t s);
 int tree_fan_in(int family);  // triangles folded per tree CTA
 cudaError_t launch_tree_batched(const TreeCta* desc, int nctas, int family, cudaStream_t s);
 

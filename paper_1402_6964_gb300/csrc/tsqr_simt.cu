@@ -374,6 +374,15 @@ int choose_streams(int n, int k, int fp64, int tc, int64_t m)
         }
         return std::max(w, (P + w - 1) / w * w);
     }
+    if (!fp64 && cta_leaf_supported(n, k)) {
+        int P = num_sms() * std::min(8, cta_leaf_ctas_per_sm(n, k));
+        if (m > 0) {
+            const int64_t minrows = 4 * (int64_t)cta_leaf_rows_per_tile();
+            const int64_t cap = std::max<int64_t>(1, (m + minrows - 1) / minrows);
+            P = (int)std::min<int64_t>(P, cap);
+        }
+        return std::max(P, 1);
+    }
     // CTA-per-stream kernel: enough resident CTAs to keep the SIMT pipes
     // issuing while each stream waits at its per-column barrier, but no more:
     // every extra stream adds a triangle to the tree.
@@ -438,6 +447,11 @@ cudaError_t pass_push(PassState& st, const void* X, int64_t rows, int64_t ldx, i
         // projection-only pass on the tensor cores
         e = launch_gp_tc(static_cast<const float*>(X), rows, ldx, st.n, st.k, st.rows_seen, st.seed, st.P, st.cs,
                          st.gx, status, s);
+    } else if (!st.fp64 && !xf64 && qr && cta_leaf_supported(st.n, st.k)) {
+        const int L = cta_leaf_rows_per_tile();
+        int64_t pw = (rows + st.P - 1) / st.P;
+        a.rows_per_cta = ((pw + L - 1) / L) * L;
+        e = launch_cta_leaf(a, st.P, s);
     } else if (warp_path) {
         const int L = warp_leaf_rows_per_tile(st.n);
         int64_t pw = (rows + st.P - 1) / st.P;

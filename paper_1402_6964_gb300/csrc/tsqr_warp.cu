@@ -552,6 +552,257 @@ cudaError_t launch_tree_wide(const float* Rin, int P_in, int n, float* Rout, cud
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// CTA-per-stream leaf for 64 < n <= 256 in binary32.  Thread c owns column c:
+// the 32 rows of each tile for that column sit in its registers, so all dot
+// products are thread-local; the running triangle (packed) is in shared
+// memory.  One barrier per column step: the owner of column j+1 publishes the
+// column's raw values, its squared norm and R(j+1, j+1) right after its own
+// update in step j, so step j+1 can start with everything it needs.
+constexpr int kCtaRows = 32;
+
+__host__ __device__ inline size_t cta_smem_bytes(int n, int k)
+{
+    const int kp = (k + 3) & ~3;
+    size_t b = 128;                                          // mbarrier
+    b += up(sizeof(float) * (size_t)kCtaRows * n, 128);      // TMA staging tile
+    b += up(sizeof(float) * (size_t)(n * (n + 1) / 2), 16);  // packed R
+    b += sizeof(float) * 2 * (kCtaRows + 4);                 // published column (+ sigma, alpha)
+    b += sizeof(float) * (size_t)kp * kCtaRows;              // Gaussian tile
+    b += sizeof(float) * (size_t)kp * n;                     // projection accumulators
+    return up(b, 128);
+}
+
+template <bool GP>
+__global__ void __launch_bounds__(256) tsqr_cta_kernel(const LeafArgs a)
+{
+    constexpr int L = kCtaRows;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int n = a.n;
+    const int k = GP ? a.k : 0;
+    const int kp = (k + 3) & ~3;
+    const int c = threadIdx.x, nt = blockDim.x;
+    const bool own = c < n;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    float* tile = reinterpret_cast<float*>(smem + 128);
+    float* Rs = reinterpret_cast<float*>(smem + 128 + up(sizeof(float) * (size_t)L * n, 128));
+    float* pub = Rs + up((size_t)(n * (n + 1) / 2), 4);  // [2][L + 4]: values, then sigma, alpha
+    float* gbuf = pub + 2 * (L + 4);
+    float* gxs = gbuf + (size_t)kp * L;
+    const uint32_t bar_s = smem_u32(bar);
+    const int cta = blockIdx.x;
+
+    if (c == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    {
+        const float* Rin = static_cast<const float*>(a.R_in);
+        const int nn = n * n;
+        for (int e = c; e < nn; e += nt) {
+            const int j = e / n, cc = e - j * n;
+            if (cc >= j) Rs[pk_row(j, n) + cc] = Rin ? Rin[(size_t)cta * nn + e] : 0.f;
+        }
+        for (int e = c; e < kp * n; e += nt) gxs[e] = 0.f;
+    }
+    __syncthreads();
+
+    const int64_t r0 = (int64_t)cta * a.rows_per_cta;
+    const int64_t r1 = min(a.rows, r0 + a.rows_per_cta);
+    const int64_t ntiles = r1 > r0 ? (r1 - r0 + L - 1) / L : 0;
+    const float* X = static_cast<const float*>(a.X);
+    const bool tma_ok = a.ldx == n && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    auto issue = [&](int64_t t) -> bool {
+        const int64_t row0 = r0 + t * L;
+        const int rows_v = (int)min((int64_t)L, r1 - row0);
+        const uint32_t bytes = (uint32_t)rows_v * (uint32_t)n * 4u;
+        if (!tma_ok || (bytes & 15u)) return false;
+        if (c == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_s), "r"(bytes) : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(tile)),
+                "l"(X + row0 * n), "r"(bytes), "r"(bar_s)
+                : "memory");
+        }
+        return true;
+    };
+
+    float av[L];
+    float cs_acc = 0.f;
+    bool bad = false, timed_out = false;
+    uint32_t phase = 0;
+    bool inflight = ntiles > 0 ? issue(0) : false;
+
+    for (int64_t t = 0; t < ntiles; ++t) {
+        const int64_t row0 = r0 + t * L;
+        const int rows_v = (int)min((int64_t)L, r1 - row0);
+        if (inflight) {
+            if (!__syncthreads_and(mbar_wait(bar_s, phase))) {
+                timed_out = true;
+                mbar_wait(bar_s, phase);
+                break;
+            }
+            phase ^= 1u;
+#pragma unroll
+            for (int l = 0; l < L; ++l) av[l] = (own && l < rows_v) ? tile[l * n + c] : 0.f;
+        } else {
+            const float* src = X + row0 * a.ldx;
+#pragma unroll
+            for (int l = 0; l < L; ++l) av[l] = (own && l < rows_v) ? src[(int64_t)l * a.ldx + c] : 0.f;
+        }
+        __syncthreads();
+        if (t + 1 < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            inflight = issue(t + 1);
+        } else {
+            inflight = false;
+        }
+        {
+            float s0 = 0.f;
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                bad |= !(av[l] >= 0.f);
+                s0 += av[l];
+            }
+            cs_acc += s0;
+        }
+        if (GP) {
+            const int kq = kp >> 2 > 0 ? kp >> 2 : 1;
+            for (int idx = c; idx < L * (kp >> 2); idx += nt) {
+                const int l = idx / kq, q = idx - l * kq;
+                float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (l < rows_v) g = gauss4(a.seed, a.row_base + row0 + l, (uint32_t)q);
+                gbuf[(4 * q + 0) * L + l] = g.x;
+                gbuf[(4 * q + 1) * L + l] = g.y;
+                gbuf[(4 * q + 2) * L + l] = g.z;
+                gbuf[(4 * q + 3) * L + l] = g.w;
+            }
+            __syncthreads();
+            if (own)
+                for (int q = 0; q < k; ++q) {
+                    const float4* gq = reinterpret_cast<const float4*>(gbuf + q * L);
+                    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                    for (int l4 = 0; l4 < L / 4; ++l4) {
+                        const float4 g = gq[l4];
+                        s0 = fmaf(g.x, av[4 * l4], s0);
+                        s1 = fmaf(g.y, av[4 * l4 + 1], s1);
+                        s0 = fmaf(g.z, av[4 * l4 + 2], s0);
+                        s1 = fmaf(g.w, av[4 * l4 + 3], s1);
+                    }
+                    gxs[q * n + c] += s0 + s1;
+                }
+        }
+        // column 0's owner publishes before the first step
+        if (c == 0) {
+            float sg = 0.f;
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                pub[l] = av[l];
+                sg = fmaf(av[l], av[l], sg);
+            }
+            pub[L] = sg;
+            pub[L + 1] = Rs[0];
+        }
+        for (int j = 0; j < n; ++j) {
+            __syncthreads();
+            const float* pj = pub + (j & 1) * (L + 4);
+            const float sig = pj[L], alpha = pj[L + 1];
+            const int pr = pk_row(j, n);
+            float beta = alpha;
+            if (sig > 0.f) {
+                const float nrm = sqrtf(fmaf(alpha, alpha, sig));
+                beta = alpha >= 0.f ? -nrm : nrm;
+                if (own && c > j) {
+                    const float d = alpha - beta;
+                    const float rb = __frcp_rn(beta), rd = __frcp_rn(d);
+                    const float4* p4 = reinterpret_cast<const float4*>(pj);
+                    float ga = 0.f, gb = 0.f, gc = 0.f, gd = 0.f;
+#pragma unroll
+                    for (int l4 = 0; l4 < L / 4; ++l4) {
+                        const float4 v = p4[l4];
+                        ga = fmaf(v.x, av[4 * l4], ga);
+                        gb = fmaf(v.y, av[4 * l4 + 1], gb);
+                        gc = fmaf(v.z, av[4 * l4 + 2], gc);
+                        gd = fmaf(v.w, av[4 * l4 + 3], gd);
+                    }
+                    const float g = (ga + gb) + (gc + gd);
+                    const float r = Rs[pr + c];
+                    const float wp = fmaf(d, r, g);
+                    const float f = (wp * rd) * rb;
+                    Rs[pr + c] = fmaf(wp, rb, r);
+#pragma unroll
+                    for (int l4 = 0; l4 < L / 4; ++l4) {
+                        const float4 v = p4[l4];
+                        av[4 * l4] = fmaf(f, v.x, av[4 * l4]);
+                        av[4 * l4 + 1] = fmaf(f, v.y, av[4 * l4 + 1]);
+                        av[4 * l4 + 2] = fmaf(f, v.z, av[4 * l4 + 2]);
+                        av[4 * l4 + 3] = fmaf(f, v.w, av[4 * l4 + 3]);
+                    }
+                }
+            }
+            if (c == j) Rs[pr + j] = beta;
+            // the owner of column j+1 publishes its updated column, norm and diagonal
+            if (c == j + 1 && j + 1 < n) {
+                float* pn = pub + ((j + 1) & 1) * (L + 4);
+                float sg = 0.f;
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    pn[l] = av[l];
+                    sg = fmaf(av[l], av[l], sg);
+                }
+                pn[L] = sg;
+                pn[L + 1] = Rs[pk_row(j + 1, n) + j + 1];
+            }
+        }
+        if ((t + 1) % kFlush == 0 || t + 1 == ntiles) {
+            if (own && a.cs) a.cs[(size_t)cta * n + c] += (double)cs_acc;
+            cs_acc = 0.f;
+            if (GP && a.gx && own)
+                for (int q = 0; q < k; ++q) {
+                    a.gx[((size_t)cta * k + q) * n + c] += (double)gxs[q * n + c];
+                    gxs[q * n + c] = 0.f;
+                }
+        }
+        __syncthreads();
+    }
+    if (timed_out && c == 0) set_status(a.status, MRNMF_ERR_TIMEOUT);
+    if (a.check && __syncthreads_or(bad) && c == 0) set_status(a.status, MRNMF_ERR_BAD_INPUT);
+    __syncthreads();
+    float* Rout = static_cast<float*>(a.R_out) + (size_t)cta * n * n;
+    const int nn = n * n;
+    for (int e = c; e < nn; e += nt) {
+        const int j = e / n, cc = e - j * n;
+        Rout[e] = (cc >= j) ? Rs[pk_row(j, n) + cc] : 0.f;
+    }
+}
+
+template <bool GP>
+int cta_ctas_per_sm(int n, int k)
+{
+    const size_t smem = cta_smem_bytes(n, GP ? k : 0);
+    auto kern = tsqr_cta_kernel<GP>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
+    int blocks = 0;
+    const int block = ((n + 31) / 32) * 32;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, block, smem) != cudaSuccess) return 1;
+    return blocks < 1 ? 1 : blocks;
+}
+
+template <bool GP>
+cudaError_t launch_cta(const LeafArgs& a, int grid, cudaStream_t s)
+{
+    const size_t smem = cta_smem_bytes(a.n, GP ? a.k : 0);
+    auto kern = tsqr_cta_kernel<GP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, ((a.n + 31) / 32) * 32, smem, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
 template <int NC, int L, bool GP>
 cudaError_t launch_nc(const LeafArgs& a, int streams, cudaStream_t s)
 {
@@ -640,6 +891,21 @@ cudaError_t launch_warp_batched(const BatchCta* desc, int nctas, const BatchProb
 }
 
 int warp_batched_rows_per_tile(int family) { return family == 1 ? 128 : 32; }
+
+bool cta_leaf_supported(int n, int k)
+{
+    return n > 64 && n <= 256 && k <= 64 && cta_smem_bytes(n, k) <= 220 * 1024;
+}
+
+int cta_leaf_rows_per_tile() { return kCtaRows; }
+
+int cta_leaf_ctas_per_sm(int n, int k) { return k > 0 ? cta_ctas_per_sm<true>(n, k) : cta_ctas_per_sm<false>(n, k); }
+
+cudaError_t launch_cta_leaf(const LeafArgs& a, int grid, cudaStream_t s)
+{
+    const bool gp = a.gx != nullptr && a.k > 0;
+    return gp ? launch_cta<true>(a, grid, s) : launch_cta<false>(a, grid, s);
+}
 
 int tree_fan_in(int family) { return family == 1 ? 17 : 9; }
 

@@ -159,15 +159,17 @@ def test_gauss_project_row_offset(h, oracle):
     assert np.all(np.abs(host(GX) - GXo) <= 2e-6 * _gx_bound(X, 6, 42, 10_000_000_000) + 1e-12)
 
 
-def test_fused_pass_matches_separate(h, oracle):
+@pytest.mark.parametrize("m,n,k", [(20011, 30, 12), (9001, 50, 20), (20011, 100, 40), (4003, 200, 40)])
+def test_fused_pass_matches_separate(h, oracle, m, n, k):
     # Sec. 3.5: TSQR and GP in one pass give what the two separate passes give
-    X = synth.random_nonneg(20011, 30, seed=3)
-    R, cs, GX = h.tsqr_gp(dev(X), 12, seed=99, prec="fp32")
+    X = synth.random_nonneg(m, n, seed=3 + n)
+    R, cs, GX = h.tsqr_gp(dev(X), k, seed=99, prec="fp32")
     h.sync()
     Ro = oracle.qr_r(X.astype(np.float64))
     assert rel_fro(host(R), Ro) <= R_TOL_FP32
-    GXo = oracle.gauss_project(X.astype(np.float64), 12, 99)
-    assert np.all(np.abs(host(GX) - GXo) <= 2e-6 * _gx_bound(X, 12, 99) + 1e-12)
+    GXo = oracle.gauss_project(X.astype(np.float64), k, 99)
+    assert np.all(np.abs(host(GX) - GXo) <= 2e-6 * _gx_bound(X, k, 99) + 1e-12)
+    np.testing.assert_allclose(host(cs), oracle.colsum(X.astype(np.float64)), rtol=1e-6)
 
 
 # ---------------------------------------------- the n-by-n step, same inputs
