@@ -570,13 +570,14 @@ __host__ __device__ inline size_t cta_smem_bytes(int n, int k)
     b += up(sizeof(float) * (size_t)(n * (n + 1) / 2), 16);  // packed R
     b += sizeof(float) * 2 * (kCtaRows + 4);                 // published column (+ sigma, alpha)
     b += sizeof(float) * (size_t)kp * kCtaRows;              // Gaussian tile
-    b += sizeof(float) * (size_t)kp * n;                     // projection accumulators
     return up(b, 128);
 }
 
-template <bool GP>
+// KMAX: 0 (no projection) or a bound on k; thread c keeps GX(:, c) in registers.
+template <int KMAX>
 __global__ void __launch_bounds__(256) tsqr_cta_kernel(const LeafArgs a)
 {
+    constexpr bool GP = KMAX > 0;
     constexpr int L = kCtaRows;
     extern __shared__ __align__(128) unsigned char smem[];
     const int n = a.n;
@@ -589,9 +590,11 @@ __global__ void __launch_bounds__(256) tsqr_cta_kernel(const LeafArgs a)
     float* Rs = reinterpret_cast<float*>(smem + 128 + up(sizeof(float) * (size_t)L * n, 128));
     float* pub = Rs + up((size_t)(n * (n + 1) / 2), 4);  // [2][L + 4]: values, then sigma, alpha
     float* gbuf = pub + 2 * (L + 4);
-    float* gxs = gbuf + (size_t)kp * L;
     const uint32_t bar_s = smem_u32(bar);
     const int cta = blockIdx.x;
+    float gacc[KMAX > 0 ? KMAX : 1];
+#pragma unroll
+    for (int q = 0; q < (KMAX > 0 ? KMAX : 1); ++q) gacc[q] = 0.f;
 
     if (c == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s) : "memory");
@@ -604,7 +607,6 @@ __global__ void __launch_bounds__(256) tsqr_cta_kernel(const LeafArgs a)
             const int j = e / n, cc = e - j * n;
             if (cc >= j) Rs[pk_row(j, n) + cc] = Rin ? Rin[(size_t)cta * nn + e] : 0.f;
         }
-        for (int e = c; e < kp * n; e += nt) gxs[e] = 0.f;
     }
     __syncthreads();
 
@@ -680,8 +682,9 @@ __global__ void __launch_bounds__(256) tsqr_cta_kernel(const LeafArgs a)
                 gbuf[(4 * q + 3) * L + l] = g.w;
             }
             __syncthreads();
-            if (own)
-                for (int q = 0; q < k; ++q) {
+#pragma unroll
+            for (int q = 0; q < (KMAX > 0 ? KMAX : 1); ++q) {
+                if (q < k) {
                     const float4* gq = reinterpret_cast<const float4*>(gbuf + q * L);
                     float s0 = 0.f, s1 = 0.f;
 #pragma unroll
@@ -692,8 +695,9 @@ __global__ void __launch_bounds__(256) tsqr_cta_kernel(const LeafArgs a)
                         s0 = fmaf(g.z, av[4 * l4 + 2], s0);
                         s1 = fmaf(g.w, av[4 * l4 + 3], s1);
                     }
-                    gxs[q * n + c] += s0 + s1;
+                    gacc[q] += s0 + s1;
                 }
+            }
         }
         // column 0's owner publishes before the first step
         if (c == 0) {
@@ -760,11 +764,14 @@ __global__ void __launch_bounds__(256) tsqr_cta_kernel(const LeafArgs a)
         if ((t + 1) % kFlush == 0 || t + 1 == ntiles) {
             if (own && a.cs) a.cs[(size_t)cta * n + c] += (double)cs_acc;
             cs_acc = 0.f;
-            if (GP && a.gx && own)
-                for (int q = 0; q < k; ++q) {
-                    a.gx[((size_t)cta * k + q) * n + c] += (double)gxs[q * n + c];
-                    gxs[q * n + c] = 0.f;
-                }
+            if (GP && a.gx && own) {
+#pragma unroll
+                for (int q = 0; q < (KMAX > 0 ? KMAX : 1); ++q)
+                    if (q < k) {
+                        a.gx[((size_t)cta * k + q) * n + c] += (double)gacc[q];
+                        gacc[q] = 0.f;
+                    }
+            }
         }
         __syncthreads();
     }
@@ -779,11 +786,11 @@ __global__ void __launch_bounds__(256) tsqr_cta_kernel(const LeafArgs a)
     }
 }
 
-template <bool GP>
-int cta_ctas_per_sm(int n, int k)
+template <int KMAX>
+int cta_ctas_per_sm_k(int n, int k)
 {
-    const size_t smem = cta_smem_bytes(n, GP ? k : 0);
-    auto kern = tsqr_cta_kernel<GP>;
+    const size_t smem = cta_smem_bytes(n, KMAX > 0 ? k : 0);
+    auto kern = tsqr_cta_kernel<KMAX>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
     int blocks = 0;
     const int block = ((n + 31) / 32) * 32;
@@ -791,11 +798,11 @@ int cta_ctas_per_sm(int n, int k)
     return blocks < 1 ? 1 : blocks;
 }
 
-template <bool GP>
-cudaError_t launch_cta(const LeafArgs& a, int grid, cudaStream_t s)
+template <int KMAX>
+cudaError_t launch_cta_k(const LeafArgs& a, int grid, cudaStream_t s)
 {
-    const size_t smem = cta_smem_bytes(a.n, GP ? a.k : 0);
-    auto kern = tsqr_cta_kernel<GP>;
+    const size_t smem = cta_smem_bytes(a.n, KMAX > 0 ? a.k : 0);
+    auto kern = tsqr_cta_kernel<KMAX>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, ((a.n + 31) / 32) * 32, smem, s>>>(a);
@@ -899,12 +906,21 @@ bool cta_leaf_supported(int n, int k)
 
 int cta_leaf_rows_per_tile() { return kCtaRows; }
 
-int cta_leaf_ctas_per_sm(int n, int k) { return k > 0 ? cta_ctas_per_sm<true>(n, k) : cta_ctas_per_sm<false>(n, k); }
+int cta_leaf_ctas_per_sm(int n, int k)
+{
+    if (k <= 0) return cta_ctas_per_sm_k<0>(n, 0);
+    if (k <= 16) return cta_ctas_per_sm_k<16>(n, k);
+    if (k <= 32) return cta_ctas_per_sm_k<32>(n, k);
+    return cta_ctas_per_sm_k<64>(n, k);
+}
 
 cudaError_t launch_cta_leaf(const LeafArgs& a, int grid, cudaStream_t s)
 {
-    const bool gp = a.gx != nullptr && a.k > 0;
-    return gp ? launch_cta<true>(a, grid, s) : launch_cta<false>(a, grid, s);
+    const int k = (a.gx != nullptr && a.k > 0) ? a.k : 0;
+    if (k == 0) return launch_cta_k<0>(a, grid, s);
+    if (k <= 16) return launch_cta_k<16>(a, grid, s);
+    if (k <= 32) return launch_cta_k<32>(a, grid, s);
+    return launch_cta_k<64>(a, grid, s);
 }
 
 int tree_fan_in(int family) { return family == 1 ? 17 : 9; }

@@ -145,16 +145,23 @@ def random_nonneg(m: int, n: int, seed: int, dtype=np.float32, integer: bool = F
     return g.random((m, n)).astype(dtype)
 
 
-def device_planted(m: int, n: int, r: int, seed: int, noise: float = 0.0, alpha: float = 1.0, device="cuda"):
+def device_planted(m: int, n: int, r: int, seed: int, noise: float = 0.0, alpha: float = 1.0, device="cuda",
+                   w_dist: str = "uniform", chunk: int = 0, P: Planted | None = None, out=None):
     """The planted separable X of `planted_separable` drawn on the GPU with
     torch's counter-based generator (same recipe, different stream of random
-    numbers): for workloads too large to draw on the host.  float32."""
+    numbers): for workloads too large to draw on the host.  float32.  `chunk`
+    selects an independent block of rows (same planted structure P)."""
     import torch
-    P = planted_structure(n, r, seed, alpha)
+    if P is None:
+        P = planted_structure(n, r, seed, alpha)
     g = torch.Generator(device=device)
-    g.manual_seed(int(seed) * 1000003 + 11)
-    W = torch.rand((m, r), generator=g, device=device, dtype=torch.float32)
-    X = W @ torch.from_numpy(P.Hmix.astype(np.float32)).to(device)
+    g.manual_seed(int(seed) * 1000003 + 11 + 7919 * int(chunk))
+    if w_dist == "lognormal":
+        W = torch.randn((m, r), generator=g, device=device, dtype=torch.float32).exp_()
+    else:
+        W = torch.rand((m, r), generator=g, device=device, dtype=torch.float32)
+    H = torch.from_numpy(P.Hmix.astype(np.float32)).to(device)
+    X = torch.matmul(W, H, out=out) if out is not None else W @ H
     del W
     if noise > 0:
         X.add_(torch.randn((m, n), generator=g, device=device, dtype=torch.float32), alpha=noise)
