@@ -66,11 +66,11 @@ mrnmf_status grow(mrnmf_handle* h, void** buf, size_t* have, size_t need, const 
     return MRNMF_OK;
 }
 
-int resolve_prec(int prec, int dtype, int n)
+int resolve_prec(int prec, int dtype, int n, int k)
 {
     if (prec == MRNMF_PREC_AUTO) {
         if (dtype == MRNMF_F64) return MRNMF_PREC_FP64;
-        return mrnmf::tc_supported(n) ? MRNMF_PREC_TF32X3 : MRNMF_PREC_FP32;
+        return mrnmf::tc_preferred(n, k) ? MRNMF_PREC_TF32X3 : MRNMF_PREC_FP32;
     }
     return prec;
 }
@@ -92,10 +92,10 @@ mrnmf_status check_pass_args(mrnmf_handle* h, const void* X, int64_t m, int32_t 
 // Set up h->st for a pass: precision, stream count, workspace.
 mrnmf_status setup_pass(mrnmf_handle* h, int n, int dtype, int prec, int k, uint64_t seed, int64_t m_hint)
 {
-    prec = resolve_prec(prec, dtype, n);
+    prec = resolve_prec(prec, dtype, n, k);
     if (prec == MRNMF_PREC_FP32 && dtype == MRNMF_F64)
         return fail(h, MRNMF_ERR_INVALID_ARG, "FP32 pass needs F32 input (the library never narrows X)");
-    if (prec == MRNMF_PREC_TF32X3 && (dtype != MRNMF_F32 || !mrnmf::tc_supported(n)))
+    if (prec == MRNMF_PREC_TF32X3 && (dtype != MRNMF_F32 || !mrnmf::tc_supported(n, k)))
         return fail(h, MRNMF_ERR_INVALID_ARG, "TF32X3 pass needs F32 input and a supported n");
     mrnmf::PassState st;
     st.n = n;

@@ -68,7 +68,8 @@ cudaError_t residual(const double* R, int n, const int32_t* K, int r, const doub
                      cudaStream_t s);
 
 // ---- tensor-core leaf (tsqr_tc.cu) ----
-bool tc_supported(int n);
+bool tc_supported(int n, int k);   // the TF32X3 pass exists for this shape
+bool tc_preferred(int n, int k);   // and MRNMF_PREC_AUTO picks it
 
 // ---- tensor-core Gaussian projection pass (gp_tc.cu) ----
 bool gp_tc_supported(int n, int k);

@@ -63,7 +63,12 @@ bool cta_leaf_supported(int n, int k);
 int cta_leaf_rows_per_tile();
 int cta_leaf_ctas_per_sm(int n, int k);
 cudaError_t launch_cta_leaf(const LeafArgs& a, int grid, cudaStream_t s);
-int tree_fan_in(int family);  // triangles folded per tree CTA
+int tree_fan_in(int family);
+
+// Tensor-core leaf (tsqr_tc.cu): 16 < n <= 64, k <= 32; one stream per CTA.
+int tc_leaf_rows_per_tile();
+int tc_leaf_ctas_per_sm();
+cudaError_t launch_tc_leaf(const LeafArgs& a, int grid, cudaStream_t s);  // triangles folded per tree CTA
 cudaError_t launch_tree_batched(const TreeCta* desc, int nctas, int family, cudaStream_t s);
 
 // Wide tree level (binary32, n <= 64): P_in triangles -> *P_out = ceil(P_in / (S+1)).

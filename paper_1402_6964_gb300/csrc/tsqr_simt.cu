@@ -362,7 +362,16 @@ void pass_state_carve(PassState& st, void* base)
 
 int choose_streams(int n, int k, int fp64, int tc, int64_t m)
 {
-    (void)tc;
+    if (tc && !fp64) {
+        // one stream per CTA, one CTA per SM
+        int P = num_sms() * tc_leaf_ctas_per_sm();
+        if (m > 0) {
+            const int64_t minrows = 2 * (int64_t)tc_leaf_rows_per_tile();
+            const int64_t cap = std::max<int64_t>(1, (m + minrows - 1) / minrows);
+            P = (int)std::min<int64_t>(P, cap);
+        }
+        return std::max(P, 1);
+    }
     if (!fp64 && warp_leaf_supported(n, k)) {
         // one stream per warp; as many warps as the SM holds at once
         const int w = warp_leaf_warps_per_cta();
@@ -447,6 +456,11 @@ cudaError_t pass_push(PassState& st, const void* X, int64_t rows, int64_t ldx, i
         // projection-only pass on the tensor cores
         e = launch_gp_tc(static_cast<const float*>(X), rows, ldx, st.n, st.k, st.rows_seen, st.seed, st.P, st.cs,
                          st.gx, status, s);
+    } else if (st.tc && !xf64 && qr) {
+        const int L = tc_leaf_rows_per_tile();
+        int64_t pw = (rows + st.P - 1) / st.P;
+        a.rows_per_cta = ((pw + L - 1) / L) * L;
+        e = launch_tc_leaf(a, st.P, s);
     } else if (!st.fp64 && !xf64 && qr && cta_leaf_supported(st.n, st.k)) {
         const int L = cta_leaf_rows_per_tile();
         int64_t pw = (rows + st.P - 1) / st.P;
