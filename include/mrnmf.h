@@ -54,10 +54,13 @@ typedef enum {
 typedef enum { MRNMF_F32 = 0, MRNMF_F64 = 1 } mrnmf_dtype;
 
 /* Arithmetic of the pass.  FP64: everything in binary64 (X must be F64).
- * FP32: binary32 SIMT Householder.  TF32X3: binary32 reflectors with the
- * blocked trailing update on tcgen05 tensor cores in 3-pass split TF32
- * (hi*hi + hi*lo + lo*hi), FP32 accumulation.  AUTO picks FP64 for F64
- * input, otherwise the fastest form available for n. */
+ * FP32: binary32 SIMT Householder.  TF32X3 (F32 input, 16 < n <= 64,
+ * k <= 32, else MRNMF_ERR_INVALID_ARG): binary32 reflectors in 16-column
+ * panels with the compact-WY trailing update and the Gaussian projection on
+ * tcgen05 tensor cores in 3-pass split TF32 (hi*hi + hi*lo + lo*hi), FP32
+ * accumulation; R within 1e-5 of the FP64 oracle but about 30x the FP32
+ * form's error, and slower than FP32 on GB300, so AUTO does not pick it.
+ * AUTO picks FP64 for F64 input, otherwise FP32. */
 typedef enum { MRNMF_PREC_AUTO = 0, MRNMF_PREC_FP64 = 1, MRNMF_PREC_FP32 = 2, MRNMF_PREC_TF32X3 = 3 } mrnmf_prec;
 
 typedef enum { MRNMF_SPA = 0, MRNMF_XRAY = 1, MRNMF_GP = 2 } mrnmf_method;
