@@ -575,7 +575,7 @@ __host__ __device__ inline size_t cta_smem_bytes(int n, int k)
 
 // KMAX: 0 (no projection) or a bound on k; thread c keeps GX(:, c) in registers.
 template <int KMAX>
-__global__ void __launch_bounds__(256) tsqr_cta_kernel(const LeafArgs a)
+__global__ void __launch_bounds__(256, KMAX <= 48 ? 2 : 1) tsqr_cta_kernel(const LeafArgs a)
 {
     constexpr bool GP = KMAX > 0;
     constexpr int L = kCtaRows;
@@ -585,6 +585,7 @@ __global__ void __launch_bounds__(256) tsqr_cta_kernel(const LeafArgs a)
     const int kp = (k + 3) & ~3;
     const int c = threadIdx.x, nt = blockDim.x;
     const bool own = c < n;
+    const int last_col = (c | 31);  // highest column of this warp
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     float* tile = reinterpret_cast<float*>(smem + 128);
     float* Rs = reinterpret_cast<float*>(smem + 128 + up(sizeof(float) * (size_t)L * n, 128));
@@ -699,19 +700,25 @@ __global__ void __launch_bounds__(256) tsqr_cta_kernel(const LeafArgs a)
                 }
             }
         }
-        // column 0's owner publishes before the first step
-        if (c == 0) {
-            float sg = 0.f;
+        // The owner of a column publishes its values, squared norm and
+        // diagonal entry of R (column 0's owner before the first step).
+        auto publish = [&](float* pn, float rjj) {
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
-            for (int l = 0; l < L; ++l) {
-                pub[l] = av[l];
-                sg = fmaf(av[l], av[l], sg);
+            for (int l4 = 0; l4 < L / 4; ++l4) {
+                reinterpret_cast<float4*>(pn)[l4] = make_float4(av[4 * l4], av[4 * l4 + 1], av[4 * l4 + 2], av[4 * l4 + 3]);
+                s0 = fmaf(av[4 * l4], av[4 * l4], s0);
+                s1 = fmaf(av[4 * l4 + 1], av[4 * l4 + 1], s1);
+                s2 = fmaf(av[4 * l4 + 2], av[4 * l4 + 2], s2);
+                s3 = fmaf(av[4 * l4 + 3], av[4 * l4 + 3], s3);
             }
-            pub[L] = sg;
-            pub[L + 1] = Rs[0];
-        }
+            pn[L] = (s0 + s1) + (s2 + s3);
+            pn[L + 1] = rjj;
+        };
+        if (c == 0) publish(pub, Rs[0]);
         for (int j = 0; j < n; ++j) {
             __syncthreads();
+            if (last_col < j) continue;  // every column of this warp is finished
             const float* pj = pub + (j & 1) * (L + 4);
             const float sig = pj[L], alpha = pj[L + 1];
             const int pr = pk_row(j, n);
@@ -749,17 +756,7 @@ __global__ void __launch_bounds__(256) tsqr_cta_kernel(const LeafArgs a)
             }
             if (c == j) Rs[pr + j] = beta;
             // the owner of column j+1 publishes its updated column, norm and diagonal
-            if (c == j + 1 && j + 1 < n) {
-                float* pn = pub + ((j + 1) & 1) * (L + 4);
-                float sg = 0.f;
-#pragma unroll
-                for (int l = 0; l < L; ++l) {
-                    pn[l] = av[l];
-                    sg = fmaf(av[l], av[l], sg);
-                }
-                pn[L] = sg;
-                pn[L + 1] = Rs[pk_row(j + 1, n) + j + 1];
-            }
+            if (c == j + 1 && j + 1 < n) publish(pub + ((j + 1) & 1) * (L + 4), Rs[pk_row(j + 1, n) + j + 1]);
         }
         if ((t + 1) % kFlush == 0 || t + 1 == ntiles) {
             if (own && a.cs) a.cs[(size_t)cta * n + c] += (double)cs_acc;
@@ -792,6 +789,7 @@ int cta_ctas_per_sm_k(int n, int k)
     const size_t smem = cta_smem_bytes(n, KMAX > 0 ? k : 0);
     auto kern = tsqr_cta_kernel<KMAX>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     int blocks = 0;
     const int block = ((n + 31) / 32) * 32;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, block, smem) != cudaSuccess) return 1;
@@ -804,6 +802,8 @@ cudaError_t launch_cta_k(const LeafArgs& a, int grid, cudaStream_t s)
     const size_t smem = cta_smem_bytes(a.n, KMAX > 0 ? a.k : 0);
     auto kern = tsqr_cta_kernel<KMAX>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     kern<<<grid, ((a.n + 31) / 32) * 32, smem, s>>>(a);
     count_launch();
@@ -911,6 +911,7 @@ int cta_leaf_ctas_per_sm(int n, int k)
     if (k <= 0) return cta_ctas_per_sm_k<0>(n, 0);
     if (k <= 16) return cta_ctas_per_sm_k<16>(n, k);
     if (k <= 32) return cta_ctas_per_sm_k<32>(n, k);
+    if (k <= 48) return cta_ctas_per_sm_k<48>(n, k);
     return cta_ctas_per_sm_k<64>(n, k);
 }
 
@@ -920,6 +921,7 @@ cudaError_t launch_cta_leaf(const LeafArgs& a, int grid, cudaStream_t s)
     if (k == 0) return launch_cta_k<0>(a, grid, s);
     if (k <= 16) return launch_cta_k<16>(a, grid, s);
     if (k <= 32) return launch_cta_k<32>(a, grid, s);
+    if (k <= 48) return launch_cta_k<48>(a, grid, s);
     return launch_cta_k<64>(a, grid, s);
 }
 
