@@ -339,6 +339,23 @@ __global__ void __launch_bounds__(32) nnls_lh_smem_kernel(const double* __restri
 // Cholesky or triangular solve has O(p) latency instead of O(p^2).
 __device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
+// 1/sqrt(d) for d > 0 in binary64 without a binary64 square root or division
+// (both are long sequences on GB300's reduced-rate binary64 pipe): a binary32
+// seed, then two Newton steps y <- y + y (1 - d y^2) / 2, each of which about
+// doubles the correct bits (2^-22 -> 2^-44 -> rounding level).  Outside the
+// binary32 range of the seed the plain expression is used.
+__device__ __forceinline__ double rsqrt_d(double d)
+{
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+    double y = (double)rsqrtf((float)d);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double e = fma(-d * y, y, 1.0);
+        y = fma(0.5 * y, e, y);
+    }
+    return y;
+}
+
 __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restrict__ AtA_g,
                                                            const double* __restrict__ Atb,
                                                            const double* __restrict__ btb, int r, int n,
@@ -360,6 +377,116 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
     double x = 0.0;
     bool passive = false;
     int st = 0;
+    // Cholesky factor of A^T A over the passive set, in factor order.  Lane k
+    // (k < p) holds the k-th factor index idx, row k of L (Lrow[q] = L(k,q),
+    // q < k), column k below the diagonal (Lcol[a] = L(a,k), a > k) and
+    // 1/L(k,k); coefficient lane i holds its factor position `my` (or -1).
+    // An entering index appends one row (forward substitution, O(p) dependent
+    // steps); an index leaving the passive set triggers a full refactor.
+    double Lrow[32], Lcol[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        Lrow[q] = 0.0;
+        Lcol[q] = 0.0;
+    }
+    double invd = 0.0;
+    int idx = 0, my = -1, p = 0;
+
+    auto refactor = [&]() -> bool {
+        const unsigned pm = __ballot_sync(FULL, act && passive);
+        p = __popc(pm);
+        my = act && passive ? __popc(pm & ((1u << lane) - 1u)) : -1;  // passive indices in increasing order
+        {
+            unsigned m = pm;
+            for (int k = 0; k < lane && m; ++k) m &= m - 1;
+            idx = m ? __ffs(m) - 1 : 0;
+        }
+        const bool in = lane < p;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            Lrow[q] = 0.0;
+            Lcol[q] = 0.0;
+        }
+        invd = 0.0;
+        bool ok = true;
+        // right-looking Cholesky of AtA[idx, idx]
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            if (k >= p) break;
+            const int ik = __shfl_sync(FULL, idx, k);
+            double d = 0.0;
+            if (lane == k) {
+                d = AtA[idx * r + idx];
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    if (q < k) d -= Lrow[q] * Lrow[q];
+            }
+            d = shfl_d(d, k);
+            if (!(d > 0.0)) {
+                ok = false;
+                break;
+            }
+            const double ik_inv = rsqrt_d(d);
+            if (lane == k) invd = ik_inv;
+            // L(a,k) for a > k: (A(a,k) - sum_{q<k} L(a,q) L(k,q)) / L(k,k)
+            double s = (in && lane > k) ? AtA[idx * r + ik] : 0.0;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                if (q < k) {
+                    const double lkq = shfl_d(Lrow[q], k);
+                    s -= Lrow[q] * lkq;
+                }
+            }
+            const double lak = (in && lane > k) ? s * ik_inv : 0.0;
+            if (in && lane > k) Lrow[k] = lak;
+            // lane k collects its column: L(a,k) for a > k
+#pragma unroll
+            for (int a = 0; a < 32; ++a) {
+                if (a > k && a < p) {
+                    const double v = shfl_d(lak, a);
+                    if (lane == k) Lcol[a] = v;
+                }
+            }
+        }
+        return ok;
+    };
+
+    // Append index bi to the factor: row p of L solves L l = AtA(idx, bi)
+    // (same formula and summation order as the refactor's row p).
+    auto add_index = [&](int bi) -> bool {
+        double b = lane < p ? AtA[idx * r + bi] : 0.0;
+        double l = 0.0;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            if (q >= p) break;
+            if (lane == q) l = b * invd;
+            const double lq = shfl_d(l, q);
+            if (lane > q && lane < p) b -= Lrow[q] * lq;
+            if (lane == p) Lrow[q] = lq;
+        }
+        double sq = lane < p ? l * l : 0.0;
+        for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(FULL, sq, o);
+        const double d = AtA[bi * r + bi] - sq;
+        if (!(d > 0.0)) return false;
+        const double ik_inv = rsqrt_d(d);
+        if (lane == p) {
+            invd = ik_inv;
+            idx = bi;
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                if (q >= p) Lrow[q] = 0.0;
+        }
+        if (lane < p) {
+#pragma unroll
+            for (int a = 0; a < 32; ++a)
+                if (a == p) Lcol[a] = l;
+        }
+        if (lane == bi) my = p;
+        ++p;
+        return true;
+    };
+
+    bool fact_ok = true;  // the factor covers exactly the passive set
     for (int outer = 0;; ++outer) {
         // dual w = A^T b - A^T A x
         double w = rhs;
@@ -384,74 +511,13 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
             break;
         }
         if (lane == bi) passive = true;
+        if (!__all_sync(FULL, fact_ok ? add_index(bi) : refactor())) {
+            st = MRNMF_ERR_RANK_DEFICIENT;
+            break;
+        }
+        fact_ok = true;
         for (int inner = 0; inner <= r + 1; ++inner) {
-            // passive indices in increasing order; lane k of the solve <-> idx[k]
-            const unsigned pm = __ballot_sync(FULL, act && passive);
-            const int p = __popc(pm);
-            const int my = act && passive ? __popc(pm & ((1u << lane) - 1u)) : -1;  // my rank, or -1
-            // lane k takes the k-th passive index
-            int idx = 0;
-            {
-                unsigned m = pm;
-                for (int k = 0; k < lane && m; ++k) m &= m - 1;
-                idx = m ? __ffs(m) - 1 : 0;
-            }
             const bool in = lane < p;
-            double Lrow[32];
-            double Lcol[32];
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                Lrow[q] = 0.0;
-                Lcol[q] = 0.0;
-            }
-            double invd = 0.0;  // 1 / L(k,k) for this lane's row k = lane
-            bool ok = true;
-            // right-looking Cholesky of AtA[idx, idx]
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                if (k >= p) break;
-                const int ik = __shfl_sync(FULL, idx, k);
-                double d = 0.0;
-                if (lane == k) {
-                    d = AtA[idx * r + idx];
-#pragma unroll
-                    for (int q = 0; q < 32; ++q)
-                        if (q < k) d -= Lrow[q] * Lrow[q];
-                }
-                d = shfl_d(d, k);
-                if (!(d > 0.0)) {
-                    ok = false;
-                    break;
-                }
-                const double ik_inv = 1.0 / sqrt(d);
-                if (lane == k) {
-                    Lrow[k] = 1.0 / ik_inv;
-                    invd = ik_inv;
-                }
-                // L(a,k) for a > k: (A(a,k) - sum_{q<k} L(a,q) L(k,q)) / L(k,k)
-                double s = (in && lane > k) ? AtA[idx * r + ik] : 0.0;
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    if (q < k) {
-                        const double lkq = shfl_d(Lrow[q], k);
-                        s -= Lrow[q] * lkq;
-                    }
-                }
-                const double lak = (in && lane > k) ? s * ik_inv : 0.0;
-                if (in && lane > k) Lrow[k] = lak;
-                // lane k collects its column: L(a,k) for a > k
-#pragma unroll
-                for (int a = 0; a < 32; ++a) {
-                    if (a > k && a < p) {
-                        const double v = shfl_d(lak, a);
-                        if (lane == k) Lcol[a] = v;
-                    }
-                }
-            }
-            if (!__all_sync(FULL, ok)) {
-                st = MRNMF_ERR_RANK_DEFICIENT;
-                break;
-            }
             // forward solve L y = rhs[idx]
             const double bk = shfl_d(rhs, idx);  // lane k: rhs of its passive index (lanes >= p: junk, unused)
             double acc = 0.0, y = 0.0;
@@ -513,6 +579,11 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
             }
             if (inner == r + 1) {
                 st = MRNMF_ERR_NOT_CONVERGED;
+                break;
+            }
+            // some coefficients left the passive set
+            if (!__all_sync(FULL, refactor())) {
+                st = MRNMF_ERR_RANK_DEFICIENT;
                 break;
             }
         }
