@@ -101,91 +101,146 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
                 make_float4(a0[4 * l4], a0[4 * l4 + 1], a0[4 * l4 + 2], a0[4 * l4 + 3]);
     }
     __syncwarp();
-    for (int j = 0; j < n; ++j) {
-        const float4* pj = reinterpret_cast<const float4*>(pub + (j & 1) * L);
-        const bool act0 = j < 32;  // set 0 still holds columns >= j
-        float g0a = 0.f, g0b = 0.f, g0c = 0.f, g0d = 0.f, g1a = 0.f, g1b = 0.f, g1c = 0.f, g1d = 0.f;
+    // beta = -sign(alpha) sqrt(alpha^2 + sigma), d = alpha - beta.  With
+    // w' = d R_jc + g_c (= d w), the reflector's action is
+    // R_jc -= tau w  =  R_jc + w'/beta  and
+    // A(:,c) -= tau s w A(:,j)  =  A(:,c) + (w'/d)(1/beta) A(:,j).
+    // Reciprocals of beta and d (never of their product, which can
+    // underflow for a column already annihilated to rounding level).  The
+    // square root and the reciprocals are correctly rounded: each stream's R
+    // takes tens of thousands of reflectors, and a beta a few ulp off makes
+    // each of them slightly non-orthogonal (measured: R error 13x larger with
+    // the SFU approximations at 1e7 x 50).
+    int j = 0;
+    if (NC == 2) {
+        // two live columns per lane while more than 32 columns remain (j < n - 32 <= 32)
+        const int jm = n - 32;
+        for (; j < jm; ++j) {
+            const float4* pj = reinterpret_cast<const float4*>(pub + (j & 1) * L);
+            float g0a = 0.f, g0b = 0.f, g0c = 0.f, g0d = 0.f, g1a = 0.f, g1b = 0.f, g1c = 0.f, g1d = 0.f;
 #pragma unroll
-        for (int l4 = 0; l4 < L / 4; ++l4) {
-            const float4 v = pj[l4];
-            if (act0) {
+            for (int l4 = 0; l4 < L / 4; ++l4) {
+                const float4 v = pj[l4];
                 g0a = fmaf(v.x, a0[4 * l4], g0a);
                 g0b = fmaf(v.y, a0[4 * l4 + 1], g0b);
                 g0c = fmaf(v.z, a0[4 * l4 + 2], g0c);
                 g0d = fmaf(v.w, a0[4 * l4 + 3], g0d);
-            }
-            if (NC == 2) {
                 g1a = fmaf(v.x, a1[4 * l4], g1a);
                 g1b = fmaf(v.y, a1[4 * l4 + 1], g1b);
                 g1c = fmaf(v.z, a1[4 * l4 + 2], g1c);
                 g1d = fmaf(v.w, a1[4 * l4 + 3], g1d);
             }
-        }
-        const float g0 = (g0a + g0b) + (g0c + g0d), g1 = (g1a + g1b) + (g1c + g1d);
-        const float sig = __shfl_sync(FULL, act0 ? g0 : g1, j & 31);
-        const int pr = pk_row(j, n);
-        const float alpha = Rw[pr + j];
-        __syncwarp();
-        // beta = -sign(alpha) sqrt(alpha^2 + sigma), d = alpha - beta.  With
-        // w' = d R_jc + g_c (= d w), the reflector's action is
-        // R_jc -= tau w  =  R_jc + w'/beta  and
-        // A(:,c) -= tau s w A(:,j)  =  A(:,c) + (w'/d)(1/beta) A(:,j).
-        // Reciprocals of beta and d (never of their product, which can
-        // underflow for a column already annihilated to rounding level).
-        float beta = alpha;
-        if (sig > 0.f) {
-            const float nrm = sqrtf(fmaf(alpha, alpha, sig));
-            beta = alpha >= 0.f ? -nrm : nrm;
-            const float d = alpha - beta;
-            const float rb = __frcp_rn(beta), rd = __frcp_rn(d);
-            float f0 = 0.f, f1 = 0.f;
-            if (act0 && own0 && c0 > j) {
-                const float r = Rw[pr + c0];
-                const float wp = fmaf(d, r, g0);
-                f0 = (wp * rd) * rb;
-                Rw[pr + c0] = fmaf(wp, rb, r);
-            }
-            if (NC == 2 && own1 && c1 > j) {
-                const float r = Rw[pr + c1];
-                const float wp = fmaf(d, r, g1);
-                f1 = (wp * rd) * rb;
-                Rw[pr + c1] = fmaf(wp, rb, r);
-            }
+            const float g0 = (g0a + g0b) + (g0c + g0d), g1 = (g1a + g1b) + (g1c + g1d);
+            const float sig = __shfl_sync(FULL, g0, j);
+            const int pr = pk_row(j, n);
+            const float alpha = Rw[pr + j];
+            __syncwarp();
+            float beta = alpha;
+            if (sig > 0.f) {
+                const float nrm = sqrtf(fmaf(alpha, alpha, sig));
+                beta = alpha >= 0.f ? -nrm : nrm;
+                const float d = alpha - beta;
+                const float rb = __frcp_rn(beta), rd = __frcp_rn(d);
+                float f0 = 0.f, f1 = 0.f;
+                if (own0 && c0 > j) {
+                    const float r = Rw[pr + c0];
+                    const float wp = fmaf(d, r, g0);
+                    f0 = (wp * rd) * rb;
+                    Rw[pr + c0] = fmaf(wp, rb, r);
+                }
+                if (own1) {
+                    const float r = Rw[pr + c1];
+                    const float wp = fmaf(d, r, g1);
+                    f1 = (wp * rd) * rb;
+                    Rw[pr + c1] = fmaf(wp, rb, r);
+                }
 #pragma unroll
-            for (int l4 = 0; l4 < L / 4; ++l4) {
-                const float4 v = pj[l4];
-                if (act0) {
+                for (int l4 = 0; l4 < L / 4; ++l4) {
+                    const float4 v = pj[l4];
                     a0[4 * l4] = fmaf(f0, v.x, a0[4 * l4]);
                     a0[4 * l4 + 1] = fmaf(f0, v.y, a0[4 * l4 + 1]);
                     a0[4 * l4 + 2] = fmaf(f0, v.z, a0[4 * l4 + 2]);
                     a0[4 * l4 + 3] = fmaf(f0, v.w, a0[4 * l4 + 3]);
-                }
-                if (NC == 2) {
                     a1[4 * l4] = fmaf(f1, v.x, a1[4 * l4]);
                     a1[4 * l4 + 1] = fmaf(f1, v.y, a1[4 * l4 + 1]);
                     a1[4 * l4 + 2] = fmaf(f1, v.z, a1[4 * l4 + 2]);
                     a1[4 * l4 + 3] = fmaf(f1, v.w, a1[4 * l4 + 3]);
                 }
             }
+            if (lane == j) Rw[pr + j] = beta;
+            // the owner of column j+1 publishes its updated values
+            const int jn = j + 1;
+            if (lane == (jn & 31)) {
+                float4* dst = reinterpret_cast<float4*>(pub + (jn & 1) * L);
+                if (jn < 32) {
+#pragma unroll
+                    for (int l4 = 0; l4 < L / 4; ++l4)
+                        dst[l4] = make_float4(a0[4 * l4], a0[4 * l4 + 1], a0[4 * l4 + 2], a0[4 * l4 + 3]);
+                } else {
+#pragma unroll
+                    for (int l4 = 0; l4 < L / 4; ++l4)
+                        dst[l4] = make_float4(a1[4 * l4], a1[4 * l4 + 1], a1[4 * l4 + 2], a1[4 * l4 + 3]);
+                }
+            }
+            __syncwarp();
+        }
+        // from here on the live columns are jm .. jm+31, one per lane: the
+        // lanes whose first column is finished move their second into slot 0
+        if (lane < jm) {
+#pragma unroll
+            for (int l = 0; l < L; ++l) a0[l] = a1[l];
+        }
+    }
+    const int cm = (NC == 2 && lane < n - 32) ? lane + 32 : lane;  // the lane's live column
+    const bool om = NC == 2 ? true : own0;
+    for (; j < n; ++j) {
+        const float4* pj = reinterpret_cast<const float4*>(pub + (j & 1) * L);
+        float g0a = 0.f, g0b = 0.f, g0c = 0.f, g0d = 0.f;
+#pragma unroll
+        for (int l4 = 0; l4 < L / 4; ++l4) {
+            const float4 v = pj[l4];
+            g0a = fmaf(v.x, a0[4 * l4], g0a);
+            g0b = fmaf(v.y, a0[4 * l4 + 1], g0b);
+            g0c = fmaf(v.z, a0[4 * l4 + 2], g0c);
+            g0d = fmaf(v.w, a0[4 * l4 + 3], g0d);
+        }
+        const float g0 = (g0a + g0b) + (g0c + g0d);
+        const float sig = __shfl_sync(FULL, g0, j & 31);
+        const int pr = pk_row(j, n);
+        const float alpha = Rw[pr + j];
+        __syncwarp();
+        float beta = alpha;
+        if (sig > 0.f) {
+            const float nrm = sqrtf(fmaf(alpha, alpha, sig));
+            beta = alpha >= 0.f ? -nrm : nrm;
+            const float d = alpha - beta;
+            const float rb = __frcp_rn(beta), rd = __frcp_rn(d);
+            float f0 = 0.f;
+            if (om && cm > j) {
+                const float r = Rw[pr + cm];
+                const float wp = fmaf(d, r, g0);
+                f0 = (wp * rd) * rb;
+                Rw[pr + cm] = fmaf(wp, rb, r);
+            }
+#pragma unroll
+            for (int l4 = 0; l4 < L / 4; ++l4) {
+                const float4 v = pj[l4];
+                a0[4 * l4] = fmaf(f0, v.x, a0[4 * l4]);
+                a0[4 * l4 + 1] = fmaf(f0, v.y, a0[4 * l4 + 1]);
+                a0[4 * l4 + 2] = fmaf(f0, v.z, a0[4 * l4 + 2]);
+                a0[4 * l4 + 3] = fmaf(f0, v.w, a0[4 * l4 + 3]);
+            }
         }
         if (lane == (j & 31)) Rw[pr + j] = beta;
-        // the owner of column j+1 publishes its updated values
         const int jn = j + 1;
         if (jn < n && lane == (jn & 31)) {
             float4* dst = reinterpret_cast<float4*>(pub + (jn & 1) * L);
-            if (jn < 32) {
 #pragma unroll
-                for (int l4 = 0; l4 < L / 4; ++l4)
-                    dst[l4] = make_float4(a0[4 * l4], a0[4 * l4 + 1], a0[4 * l4 + 2], a0[4 * l4 + 3]);
-            } else if (NC == 2) {
-#pragma unroll
-                for (int l4 = 0; l4 < L / 4; ++l4)
-                    dst[l4] = make_float4(a1[4 * l4], a1[4 * l4 + 1], a1[4 * l4 + 2], a1[4 * l4 + 3]);
-            }
+            for (int l4 = 0; l4 < L / 4; ++l4)
+                dst[l4] = make_float4(a0[4 * l4], a0[4 * l4 + 1], a0[4 * l4 + 2], a0[4 * l4 + 3]);
         }
         __syncwarp();
     }
-
 }
 
 template <int NC, int L, bool GP>
