@@ -168,6 +168,42 @@ mrnmf_status mrnmf_rank_sweep(mrnmf_handle* handle, int32_t method, const double
                               double* curve, void* stream);
 
 /*
+ * Follow-ups that read X a second time (optional: the method itself needs
+ * only the one pass).
+ *
+ * mrnmf_gather_columns: W = X(:,K), the left factor of X ~ X(:,K) H (Sec. 2).
+ *   X  device m-by-n row-major (ldx >= n), F32 or F64
+ *   K  device r int32, each in [0, n)      W device m-by-r row-major (ldw >= r), same dtype as X
+ * A K entry outside [0, n) sets MRNMF_ERR_INVALID_ARG on the device (column 0
+ * is read in its place).  Bit-exact copy.
+ *
+ * mrnmf_full_residual: out[0] = ||X - X(:,K) H||_F and
+ * out[1] = ||X - X(:,K) H||_F^2 / ||X||_F^2, formed row by row from X itself
+ * (in X's precision, squares summed in binary64).  In exact arithmetic it
+ * equals mrnmf_residual on R (Sec. 2.4), so it checks the reduced
+ * computation.  H device r-by-n doubles (as from mrnmf_nnls_h), out device 2
+ * doubles; 1 <= r <= n <= 256.
+ */
+/*
+ * R-SVD form (Sec. 2.2: R = U Sigma V', so X = (QU) Sigma V'; the separable
+ * step picks the same K on Sigma V' as on R, since K is invariant under a
+ * left orthogonal factor).  One-sided Jacobi on R' in binary64.
+ *   R      device n*n doubles, row-major (any square matrix; mrnmf_tsqr_r's R)
+ *   sigma  device n doubles out, descending (nullable)
+ *   SVt    device n*n doubles out, row-major: row i = sigma_i v_i' (each row
+ *          determined up to sign)
+ * MRNMF_ERR_NOT_CONVERGED surfaces at sync if 40 sweeps do not converge.
+ */
+mrnmf_status mrnmf_r_svd(mrnmf_handle* handle, const double* R, int32_t n, double* sigma, double* SVt,
+                         void* stream);
+
+mrnmf_status mrnmf_gather_columns(mrnmf_handle* handle, const void* X, int64_t m, int32_t n, int64_t ldx,
+                                  int32_t dtype, const int32_t* K, int32_t r, void* W, int64_t ldw, void* stream);
+mrnmf_status mrnmf_full_residual(mrnmf_handle* handle, const void* X, int64_t m, int32_t n, int64_t ldx,
+                                 int32_t dtype, const int32_t* K, int32_t r, const double* H, double* out,
+                                 void* stream);
+
+/*
  * Streaming form of the pass (Sec. 3.4: one pass over data that arrives in
  * pieces).  begin() resets the handle's running state for n columns;
  * push() folds `rows` more rows into it (X_chunk device, row-major, ldx);

@@ -159,6 +159,8 @@ void mrnmf_destroy(mrnmf_handle* h)
         cudaFree(h->dout);
         cudaFree(h->sweep);
         cudaFree(h->bws);
+        cudaFree(h->fws);
+        cudaFree(h->svd);
         if (h->bstage) cudaFreeHost(h->bstage);
         if (h->ev_bstage) cudaEventDestroy(h->ev_bstage);
         for (int i = 0; i < 2; ++i) {

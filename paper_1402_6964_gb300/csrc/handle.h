@@ -40,6 +40,12 @@ struct mrnmf_handle {
     void* bstage = nullptr;
     size_t bstage_bytes = 0;
     cudaEvent_t ev_bstage = nullptr;
+    // follow-ups (second read of X): per-block partial sums of the full-space residual
+    void* fws = nullptr;
+    size_t fws_bytes = 0;
+    // R-SVD scratch
+    void* svd = nullptr;
+    size_t svd_bytes = 0;
 };
 
 namespace mrnmf {

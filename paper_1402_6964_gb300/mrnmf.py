@@ -28,7 +28,8 @@ EXPORTS = [
     "mrnmf_gauss_project", "mrnmf_tsqr_gp", "mrnmf_select_extreme", "mrnmf_nnls_h", "mrnmf_residual",
     "mrnmf_stream_begin", "mrnmf_stream_push", "mrnmf_stream_end", "mrnmf_factorize_host",
     "mrnmf_profile_events", "mrnmf_kernel_launches", "mrnmf_tsqr_r_noalloc", "mrnmf_tc_selftest",
-    "mrnmf_rank_sweep", "mrnmf_tsqr_r_batched",
+    "mrnmf_rank_sweep", "mrnmf_tsqr_r_batched", "mrnmf_gather_columns", "mrnmf_full_residual",
+    "mrnmf_r_svd",
 ]
 
 
@@ -80,6 +81,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mrnmf_tc_selftest": ([P, P, P, i32, i32, i32, P, P], st),
             "mrnmf_rank_sweep": ([P, i32, P, i32, P, P, i32, i32, P, P, P], st),
             "mrnmf_tsqr_r_batched": ([P, P, i32, P], st),
+            "mrnmf_gather_columns": ([P, P, i64, i32, i64, i32, P, i32, P, i64, P], st),
+            "mrnmf_full_residual": ([P, P, i64, i32, i64, i32, P, i32, P, P, P], st),
+            "mrnmf_r_svd": ([P, P, i32, P, P, P], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -256,6 +260,36 @@ class Handle:
         o = torch.empty(2, dtype=torch.float64, device=R.device) if out is None else out
         self.check(self._lib.mrnmf_residual(self.h, _ptr(R), n, _ptr(K), K.shape[0], _ptr(H), _ptr(o),
                                             _stream(stream)))
+        return o
+
+    def r_svd(self, R, stream=None):
+        """(sigma descending, Sigma V') of the n-by-n R (Sec. 2.2's R-SVD form)."""
+        import torch
+        n = R.shape[1]
+        sig = torch.empty(n, dtype=torch.float64, device=R.device)
+        SVt = torch.empty((n, n), dtype=torch.float64, device=R.device)
+        self.check(self._lib.mrnmf_r_svd(self.h, _ptr(R), n, _ptr(sig), _ptr(SVt), _stream(stream)))
+        return sig, SVt
+
+    def gather_columns(self, X, K, stream=None, out=None):
+        """W = X(:, K) (a second read of X)."""
+        import torch
+        _check_X(X)
+        m, n = X.shape
+        r = K.shape[0]
+        W = torch.empty((m, r), dtype=X.dtype, device=X.device) if out is None else out
+        self.check(self._lib.mrnmf_gather_columns(self.h, _ptr(X), m, n, X.stride(0), _dtype_code(X), _ptr(K), r,
+                                                  _ptr(W), W.stride(0), _stream(stream)))
+        return W
+
+    def full_residual(self, X, K, H, stream=None, out=None):
+        """(||X - X(:,K)H||_F, ||X - X(:,K)H||_F^2 / ||X||_F^2) from X itself (a second read)."""
+        import torch
+        _check_X(X)
+        m, n = X.shape
+        o = torch.empty(2, dtype=torch.float64, device=X.device) if out is None else out
+        self.check(self._lib.mrnmf_full_residual(self.h, _ptr(X), m, n, X.stride(0), _dtype_code(X), _ptr(K),
+                                                 K.shape[0], _ptr(H), _ptr(o), _stream(stream)))
         return o
 
     def rank_sweep(self, method, R=None, colsum=None, GX=None, r_max=1, stream=None):
