@@ -243,18 +243,27 @@ def run_batched(args):
 
 def run_stream(args):
     """Flow-cytometry-shaped stream (1.6e9 x 25, r = 8, log-normal W,
-    Dirichlet(0.5), sigma = 1e-2): 64M-row chunks drawn on the device one at a
-    time and pushed through mrnmf_stream_push (X is never resident whole).
-    GB/s counts the chunk reads of the pass; generation is timed apart."""
+    Dirichlet(0.5), sigma = 1e-2), or with --workload kron_fc_1p6e9x25 the
+    Kronecker-structured A kron A (A: 40,000 x 5, r_A = 4, so r = 16): 64M-row
+    chunks drawn on the device one at a time and pushed through
+    mrnmf_stream_push (X is never resident whole).  GB/s counts the chunk reads
+    of the pass; generation is timed apart."""
     import torch
 
     from paper_1402_6964_gb300 import build, mrnmf, synth
 
     build.build()
-    w = synth.WORKLOADS["fc_stream_1p6e9x25"]
+    kron = args.workload == "kron_fc_1p6e9x25"
+    w = synth.WORKLOADS["kron_fc_1p6e9x25" if kron else "fc_stream_1p6e9x25"]
     m = args.rows or w.m
     chunk = min(64 << 20, m)
-    P = synth.planted_structure(w.n, w.r, w.seed, w.alpha)
+    if kron:
+        A64, Kp = synth.kron_factor(w)
+        A = torch.from_numpy(A64.astype(np.float32)).cuda()
+        P = None
+    else:
+        P = synth.planted_structure(w.n, w.r, w.seed, w.alpha)
+        Kp = P.K
     buf = torch.empty((chunk, w.n), dtype=torch.float32, device="cuda")
     h = mrnmf.Handle()
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -265,8 +274,11 @@ def run_stream(args):
         rows = min(chunk, m - c * chunk)
         a, b, d = ev(), ev(), ev()
         a.record()
-        X, _ = synth.device_planted(rows, w.n, w.r, w.seed, noise=w.noise, alpha=w.alpha, w_dist=w.w_dist,
-                                    chunk=c, P=P, out=buf[:rows])
+        if kron:
+            X = synth.kron_rows(A, c * chunk, rows, out=buf[:rows])
+        else:
+            X, _ = synth.device_planted(rows, w.n, w.r, w.seed, noise=w.noise, alpha=w.alpha, w_dist=w.w_dist,
+                                        chunk=c, P=P, out=buf[:rows])
         b.record()
         h.stream_push(X)
         d.record()
@@ -290,7 +302,7 @@ def run_stream(args):
                       "unit": "GB/s", "ms_pass": push_ms + end_ms, "ms_generation": gen_ms, "chunks": nchunks,
                       "chunk_rows": chunk, "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm,
                                                         "unit": "GB/s", "frac": gbs / hbm, "peak_source": src},
-                      "K_spa": sorted(K.cpu().numpy().tolist()), "K_planted": P.K.tolist(),
+                      "K_spa": sorted(K.cpu().numpy().tolist()), "K_planted": Kp.tolist(),
                       "residual_rel": float(out[1].item()),
                       "config": {"workload": w.name, "m": m, "n": w.n, "r": w.r, "k": w.k}}), flush=True)
     h.close()

@@ -36,10 +36,13 @@ __global__ void gather_kernel(const T* __restrict__ X, int64_t m, int n, int64_t
     }
 }
 
-// One warp per row (grid-stride): lane l holds X(i, l + 32 s), s < NS, and
-// forms E(i, c) = X(i, c) - sum_a X(i, K[a]) H(a, c) in the input's precision;
-// squares are summed per lane, flushed to binary64 every kRowsFlush rows, and
-// reduced per block in a fixed order.
+// One warp per group of kRowsW consecutive rows (grid-stride): lane l holds
+// X(i, l + 32 s), s < NS, and forms E(i, c) = X(i, c) - sum_a X(i, K[a]) H(a, c)
+// in the input's precision (each H(a, c) read once per group); squares are
+// summed per lane, flushed to binary64 every kRowsFlush rows, and reduced per
+// block in a fixed order.
+constexpr int kRowsW = 4;
+
 template <typename T, int NS>
 __global__ void __launch_bounds__(kThreads) full_residual_kernel(const T* __restrict__ X, int64_t m, int n,
                                                                  int64_t ldx, const int32_t* __restrict__ K, int r,
@@ -61,34 +64,48 @@ __global__ void __launch_bounds__(kThreads) full_residual_kernel(const T* __rest
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t groups = (m + kRowsW - 1) / kRowsW;
     const int64_t w0 = (int64_t)blockIdx.x * (kThreads / 32) + warp, nw = (int64_t)gridDim.x * (kThreads / 32);
     double e2 = 0.0, x2 = 0.0;
     T ea = 0, xa = 0;
     int cnt = 0;
-    for (int64_t i = w0; i < m; i += nw) {
-        const T* xr = X + i * ldx;
-        T x[NS], e[NS];
+    for (int64_t gidx = w0; gidx < groups; gidx += nw) {
+        const int64_t i0 = gidx * kRowsW;
+        T e[kRowsW][NS];
+        const T* xr[kRowsW];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            const int c = lane + 32 * s;
-            x[s] = c < n ? xr[c] : (T)0;
-            e[s] = x[s];
+        for (int q = 0; q < kRowsW; ++q) {
+            const bool ok = i0 + q < m;
+            xr[q] = X + (ok ? i0 + q : i0) * ldx;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int c = lane + 32 * s;
+                e[q][s] = (ok && c < n) ? xr[q][c] : (T)0;
+            }
         }
+#pragma unroll
+        for (int q = 0; q < kRowsW; ++q)
+#pragma unroll
+            for (int s = 0; s < NS; ++s) xa = fma(e[q][s], e[q][s], xa);
         for (int a = 0; a < r; ++a) {
-            const T xk = xr[Ks[a]];
+            const int kc = Ks[a];
+            T xk[kRowsW];
+#pragma unroll
+            for (int q = 0; q < kRowsW; ++q) xk[q] = (i0 + q < m) ? xr[q][kc] : (T)0;
             const T* ha = Hs + (size_t)a * n;
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 const int c = lane + 32 * s;
-                if (c < n) e[s] = fma(-xk, ha[c], e[s]);
+                const T hv = c < n ? ha[c] : (T)0;
+#pragma unroll
+                for (int q = 0; q < kRowsW; ++q) e[q][s] = fma(-xk[q], hv, e[q][s]);
             }
         }
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            ea = fma(e[s], e[s], ea);
-            xa = fma(x[s], x[s], xa);
-        }
-        if (++cnt == kRowsFlush) {
+        for (int q = 0; q < kRowsW; ++q)
+#pragma unroll
+            for (int s = 0; s < NS; ++s) ea = fma(e[q][s], e[q][s], ea);
+        if (++cnt == kRowsFlush / kRowsW) {
             e2 += (double)ea;
             x2 += (double)xa;
             ea = xa = (T)0;

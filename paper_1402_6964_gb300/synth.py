@@ -53,7 +53,16 @@ WORKLOADS = {
                                 noise=1e-3, decades=6.0, seed=1402003),
     "fc_stream_1p6e9x25": Workload("flow-cytometry-shaped stream FP32, 1.6e9x25, r=8", 1_600_000_000, 25, 8, 16,
                                    noise=1e-2, w_dist="lognormal", alpha=0.5, seed=1402004),
+    # X = A kron A with A a 40,000 x 5 near-separable factor (r_A = 4): the
+    # structure of the flow-cytometry matrix of Sec. 5.2 (its data itself is
+    # not available); A kron A is separable with the r_A^2 = 16 columns
+    # K_A kron K_A (up to the noise in A).
+    "kron_fc_1p6e9x25": Workload("Kronecker-structured stream FP32, (4e4x5) kron (4e4x5) = 1.6e9x25, r=16",
+                                 1_600_000_000, 25, 16, 32, noise=1e-3, w_dist="lognormal", alpha=0.5,
+                                 seed=1402005),
 }
+
+KRON_FACTOR_ROWS, KRON_FACTOR_COLS, KRON_FACTOR_RANK = 40_000, 5, 4
 
 
 def _rng(*key) -> np.random.Generator:
@@ -167,3 +176,30 @@ def device_planted(m: int, n: int, r: int, seed: int, noise: float = 0.0, alpha:
         X.add_(torch.randn((m, n), generator=g, device=device, dtype=torch.float32), alpha=noise)
         X.clamp_(min=0.0)
     return X, P
+
+
+def kron_factor(w: Workload = None, rows: int = KRON_FACTOR_ROWS):
+    """The factor A (rows x 5, binary64, r_A = 4) of a Kronecker workload and
+    the planted K of A kron A: {p*5 + q : p, q in K_A}, ascending."""
+    w = w or WORKLOADS["kron_fc_1p6e9x25"]
+    A, PA = planted_separable(rows, KRON_FACTOR_COLS, KRON_FACTOR_RANK, w.seed, w.noise, w.w_dist, w.alpha,
+                              dtype=np.float64)
+    K = np.array(sorted(int(p) * KRON_FACTOR_COLS + int(q) for p in PA.K for q in PA.K), np.int32)
+    return A, K
+
+
+def kron_rows(A, start: int, count: int, out=None):
+    """Rows start .. start+count-1 of A kron A (torch tensors, any device):
+    row i*a + j (a = rows of A) is A(i,:) kron A(j,:), entry p*c + q =
+    A(i,p) A(j,q)."""
+    import torch
+    a, c = A.shape
+    idx = torch.arange(start, start + count, device=A.device, dtype=torch.int64)
+    Ai = A.index_select(0, idx // a)
+    Aj = A.index_select(0, idx % a)
+    prod = (Ai[:, :, None] * Aj[:, None, :]).reshape(count, c * c)
+    if out is None:
+        return prod
+    out.copy_(prod)
+    return out
+

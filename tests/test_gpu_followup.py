@@ -105,3 +105,30 @@ def test_full_residual_bad_index_is_reported(h):
     with pytest.raises(mrnmf.MrnmfError) as e:
         h.sync()
     assert e.value.status == mrnmf.ERR_INVALID_ARG
+
+
+def test_kron_stream_matches_oracle(h, oracle):
+    # X = A kron A (the structure of Sec. 5.2's flow-cytometry matrix), streamed in chunks
+    w = synth.WORKLOADS["kron_fc_1p6e9x25"]
+    A, Kp = synth.kron_factor(w, rows=600)
+    At = torch.from_numpy(A.astype(np.float32)).cuda()
+    m = 600 * 600
+    h.stream_begin(25, k=w.k, seed=w.seed)
+    for a in range(0, m, 100_000):
+        h.stream_push(synth.kron_rows(At, a, min(100_000, m - a)))
+    R, cs, GX = h.stream_end(25, k=w.k)
+    K, gap = h.select_extreme("spa", R=R, colsum=cs, r=16)
+    h.sync()
+    # the oracle gets the same binary32 rows the pass read (A kron A is near
+    # rank-deficient, cond ~1e6, so rounding the products differently moves
+    # R's small rows); R is checked through the Gram identity R'R = X'X
+    X64 = synth.kron_rows(torch.from_numpy(A.astype(np.float32)), 0, m).numpy().astype(np.float64)
+    Ro = oracle.qr_r(X64)
+    Rg = host(R)
+    G = X64.T @ X64
+    assert np.linalg.norm(Rg.T @ Rg - G) <= 2e-5 * np.linalg.norm(G)
+    assert np.linalg.norm(Rg.T @ Rg - Ro.T @ Ro) <= 2e-5 * np.linalg.norm(G)
+    np.testing.assert_allclose(host(cs), oracle.colsum(X64), rtol=1e-6)
+    Ko, go = oracle.spa(Ro, oracle.colsum(X64), 16)
+    assert sorted(host(K).tolist()) == sorted(Ko.tolist())
+    assert sorted(Ko.tolist()) == Kp.tolist()
