@@ -308,6 +308,22 @@ def run_stream(args):
     h.close()
 
 
+def time_over_ranks(t_local: float, world: int, device=None) -> float:
+    """The job's time: the slowest rank's timed region (max over ranks)."""
+    if world <= 1:
+        return t_local
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_gbs(bytes_per_step_per_rank: float, steps: int, world: int, t_max: float) -> float:
+    """Whole-job throughput: every rank (replica) reads its own X each step."""
+    return bytes_per_step_per_rank * steps * world / t_max / 1e9
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -374,14 +390,10 @@ def run_ours(args):
     h.sync()
     t_dev = step_ev[0].elapsed_time(step_ev[-1]) / 1e3  # seconds
     leaf_ms = [a.elapsed_time(b) for a, b in leaf_ev]
-    t_max = t_dev
-    if world > 1:
-        tt = torch.tensor([t_dev], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = time_over_ranks(t_dev, world, dev)
 
     bytes_step = 4.0 * m * n
-    value = bytes_step * args.steps * world / t_max / 1e9
+    value = job_gbs(bytes_step, args.steps, world, t_max)
     hbm, mhz, peak_src = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     leaf_s = statistics.mean(leaf_ms) / 1e3
@@ -389,13 +401,18 @@ def run_ours(args):
     flops = 2.0 * m * n * n
     simt_peak = _fp32_simt_peak_tflops(sms, mhz)
     leaf_tflops = flops / leaf_s / 1e12
+    # DRAM bytes of one leaf launch from the ncu capture recorded in
+    # profiles/leaf_traffic.json (a smaller case of the same kernel, scaled by
+    # rows); null once the kernel's source has changed since the capture
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "leaf_traffic.json")
     if os.path.exists(tfile):
         try:
+            import hashlib
             td = json.load(open(tfile))
-            if td.get("kernel_hash") == build._stamp():
-                traffic = td.get("traffic_bytes_per_launch")
+            src = open(os.path.join(ROOT, td["source"]), "rb").read()
+            if hashlib.sha256(src).hexdigest() == td["source_sha256"] and td["n"] == n and args.prec != "tf32x3":
+                traffic = td["bytes_per_row"] * m
         except Exception:
             traffic = None
     roof_hbm = {"bound": "hbm", "achieved": leaf_gbs, "peak": hbm, "unit": "GB/s", "frac": leaf_gbs / hbm,
