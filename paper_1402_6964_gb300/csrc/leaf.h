@@ -60,7 +60,7 @@ int warp_batched_rows_per_tile(int family);
 
 // CTA-per-stream leaf (tsqr_warp.cu): binary32, 64 < n <= 256.
 bool cta_leaf_supported(int n, int k);
-int cta_leaf_rows_per_tile();
+int cta_leaf_rows_per_tile(int k, int n);
 int cta_leaf_ctas_per_sm(int n, int k);
 cudaError_t launch_cta_leaf(const LeafArgs& a, int grid, cudaStream_t s);
 int tree_fan_in(int family);

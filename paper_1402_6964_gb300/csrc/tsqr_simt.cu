@@ -386,7 +386,7 @@ int choose_streams(int n, int k, int fp64, int tc, int64_t m)
     if (!fp64 && cta_leaf_supported(n, k)) {
         int P = num_sms() * std::min(8, cta_leaf_ctas_per_sm(n, k));
         if (m > 0) {
-            const int64_t minrows = 4 * (int64_t)cta_leaf_rows_per_tile();
+            const int64_t minrows = 4 * (int64_t)cta_leaf_rows_per_tile(k, n);
             const int64_t cap = std::max<int64_t>(1, (m + minrows - 1) / minrows);
             P = (int)std::min<int64_t>(P, cap);
         }
@@ -462,7 +462,7 @@ cudaError_t pass_push(PassState& st, const void* X, int64_t rows, int64_t ldx, i
         a.rows_per_cta = ((pw + L - 1) / L) * L;
         e = launch_tc_leaf(a, st.P, s);
     } else if (!st.fp64 && !xf64 && qr && cta_leaf_supported(st.n, st.k)) {
-        const int L = cta_leaf_rows_per_tile();
+        const int L = cta_leaf_rows_per_tile(a.gx ? st.k : 0, st.n);
         int64_t pw = (rows + st.P - 1) / st.P;
         a.rows_per_cta = ((pw + L - 1) / L) * L;
         e = launch_cta_leaf(a, st.P, s);

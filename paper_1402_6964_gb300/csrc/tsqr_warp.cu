@@ -615,25 +615,28 @@ cudaError_t launch_tree_wide(const float* Rin, int P_in, int n, float* Rout, cud
 // memory.  One barrier per column step: the owner of column j+1 publishes the
 // column's raw values, its squared norm and R(j+1, j+1) right after its own
 // update in step j, so step j+1 can start with everything it needs.
-constexpr int kCtaRows = 32;
+// Tile height: 64 rows without the projection while two CTAs still fit per
+// SM (n <= 184; halves the barriers and the per-column scalar work per row),
+// else 32 (the projection accumulators need the registers).
+__host__ __device__ constexpr int cta_rows(int k, int n) { return (k > 0 || n > 184) ? 32 : 64; }
 
 __host__ __device__ inline size_t cta_smem_bytes(int n, int k)
 {
     const int kp = (k + 3) & ~3;
+    const int L = cta_rows(k, n);
     size_t b = 128;                                          // mbarrier
-    b += up(sizeof(float) * (size_t)kCtaRows * n, 128);      // TMA staging tile
+    b += up(sizeof(float) * (size_t)L * n, 128);             // TMA staging tile
     b += up(sizeof(float) * (size_t)(n * (n + 1) / 2), 16);  // packed R
-    b += sizeof(float) * 2 * (kCtaRows + 4);                 // published column (+ sigma, alpha)
-    b += sizeof(float) * (size_t)kp * kCtaRows;              // Gaussian tile
+    b += sizeof(float) * 2 * (L + 4);                        // published column (+ sigma, alpha)
+    b += sizeof(float) * (size_t)kp * L;                     // Gaussian tile
     return up(b, 128);
 }
 
 // KMAX: 0 (no projection) or a bound on k; thread c keeps GX(:, c) in registers.
-template <int KMAX>
+template <int KMAX, int L>
 __global__ void __launch_bounds__(256, KMAX <= 48 ? 2 : 1) tsqr_cta_kernel(const LeafArgs a)
 {
     constexpr bool GP = KMAX > 0;
-    constexpr int L = kCtaRows;
     extern __shared__ __align__(128) unsigned char smem[];
     const int n = a.n;
     const int k = GP ? a.k : 0;
@@ -838,11 +841,11 @@ __global__ void __launch_bounds__(256, KMAX <= 48 ? 2 : 1) tsqr_cta_kernel(const
     }
 }
 
-template <int KMAX>
+template <int KMAX, int L>
 int cta_ctas_per_sm_k(int n, int k)
 {
     const size_t smem = cta_smem_bytes(n, KMAX > 0 ? k : 0);
-    auto kern = tsqr_cta_kernel<KMAX>;
+    auto kern = tsqr_cta_kernel<KMAX, L>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     int blocks = 0;
@@ -851,11 +854,11 @@ int cta_ctas_per_sm_k(int n, int k)
     return blocks < 1 ? 1 : blocks;
 }
 
-template <int KMAX>
+template <int KMAX, int L>
 cudaError_t launch_cta_k(const LeafArgs& a, int grid, cudaStream_t s)
 {
     const size_t smem = cta_smem_bytes(a.n, KMAX > 0 ? a.k : 0);
-    auto kern = tsqr_cta_kernel<KMAX>;
+    auto kern = tsqr_cta_kernel<KMAX, L>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
@@ -959,25 +962,25 @@ bool cta_leaf_supported(int n, int k)
     return n > 64 && n <= 256 && k <= 64 && cta_smem_bytes(n, k) <= 220 * 1024;
 }
 
-int cta_leaf_rows_per_tile() { return kCtaRows; }
+int cta_leaf_rows_per_tile(int k, int n) { return cta_rows(k, n); }
 
 int cta_leaf_ctas_per_sm(int n, int k)
 {
-    if (k <= 0) return cta_ctas_per_sm_k<0>(n, 0);
-    if (k <= 16) return cta_ctas_per_sm_k<16>(n, k);
-    if (k <= 32) return cta_ctas_per_sm_k<32>(n, k);
-    if (k <= 48) return cta_ctas_per_sm_k<48>(n, k);
-    return cta_ctas_per_sm_k<64>(n, k);
+    if (k <= 0) return cta_rows(0, n) == 64 ? cta_ctas_per_sm_k<0, 64>(n, 0) : cta_ctas_per_sm_k<0, 32>(n, 0);
+    if (k <= 16) return cta_ctas_per_sm_k<16, 32>(n, k);
+    if (k <= 32) return cta_ctas_per_sm_k<32, 32>(n, k);
+    if (k <= 48) return cta_ctas_per_sm_k<48, 32>(n, k);
+    return cta_ctas_per_sm_k<64, 32>(n, k);
 }
 
 cudaError_t launch_cta_leaf(const LeafArgs& a, int grid, cudaStream_t s)
 {
     const int k = (a.gx != nullptr && a.k > 0) ? a.k : 0;
-    if (k == 0) return launch_cta_k<0>(a, grid, s);
-    if (k <= 16) return launch_cta_k<16>(a, grid, s);
-    if (k <= 32) return launch_cta_k<32>(a, grid, s);
-    if (k <= 48) return launch_cta_k<48>(a, grid, s);
-    return launch_cta_k<64>(a, grid, s);
+    if (k == 0) return cta_rows(0, a.n) == 64 ? launch_cta_k<0, 64>(a, grid, s) : launch_cta_k<0, 32>(a, grid, s);
+    if (k <= 16) return launch_cta_k<16, 32>(a, grid, s);
+    if (k <= 32) return launch_cta_k<32, 32>(a, grid, s);
+    if (k <= 48) return launch_cta_k<48, 32>(a, grid, s);
+    return launch_cta_k<64, 32>(a, grid, s);
 }
 
 int tree_fan_in(int family) { return family == 1 ? 17 : 9; }
