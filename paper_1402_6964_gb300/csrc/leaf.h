@@ -65,6 +65,13 @@ int cta_leaf_ctas_per_sm(int n, int k);
 cudaError_t launch_cta_leaf(const LeafArgs& a, int grid, cudaStream_t s);
 int tree_fan_in(int family);
 
+// Warp-pipelined leaf (tsqr_pipe.cu): binary32, 64 < n <= 256, one stream per CTA.
+// MRNMF_PIPE_LEAF=0 falls back to the one-barrier-per-column CTA leaf.
+bool pipe_leaf_supported(int n, int k);
+int pipe_leaf_rows_per_tile();
+int pipe_leaf_ctas_per_sm(int n, int k);
+cudaError_t launch_pipe_leaf(const LeafArgs& a, int grid, cudaStream_t s);
+
 // Tensor-core leaf (tsqr_tc.cu): 16 < n <= 64, k <= 32; one stream per CTA.
 int tc_leaf_rows_per_tile();
 int tc_leaf_ctas_per_sm();

@@ -1,0 +1,416 @@
+// tsqr_pipe.cu -- the pass over X for 64 < n <= 256 in binary32 as a warp
+// pipeline: one CTA per row stream, warp w owns the 32-column block
+// [32w, 32w+32) of every tile, and no block-wide barrier runs per column.
+//
+// Reflector j of a tile (the column step of the local QR of Sec. 3.1 on the
+// stacked [R; A], as in the SIMT leaves) is produced by the warp that owns
+// column j: it publishes the column's values and three scalars (d = alpha -
+// beta, 1/beta, 1/d) in a shared-memory ring of tile slots.  Warp w applies,
+// in order, the reflectors of blocks 0 .. w-1 (waiting on each producer's
+// mbarrier), then performs its own 32 column steps inside the warp (only
+// __syncwarp), then signals its block.  Every thread applies the reflectors
+// to its own column in the global order (tile by tile, column by column), so
+// the arithmetic is that of the one-barrier-per-column leaf; what changes is
+// that different warps work on different tiles at the same time.
+//
+// Each column's R entries (packed triangle in shared memory) belong to the
+// column's thread.  Ring slots are reused after every consumer warp has
+// signalled the slot's "free" mbarrier.  Every wait is bounded (1 s); the
+// first warp that gives up raises a CTA-wide abort flag that ends every
+// other wait at once, and MRNMF_ERR_TIMEOUT is reported.
+//
+// Column sums and the Gaussian projection (Algorithm 1, Sec. 3.2) are folded
+// in: warp 0 draws each tile's G into the slot, every thread accumulates
+// G' A(:, c) for its column in binary32, flushed to binary64 every kFlush
+// tiles.
+#include <cstdlib>
+
+#include "common.cuh"
+#include "internal.h"
+#include "leaf.h"
+
+namespace mrnmf {
+
+namespace {
+
+constexpr int kL = 32;          // tile height
+constexpr int kD = 2;           // ring slots (tiles in flight)
+constexpr int kRS = kL + 4;     // ring entry: L values, then d, 1/beta, 1/d, pad
+constexpr int kMaxW = 8;        // warps (n <= 256)
+constexpr int kFlushT = 32;     // tiles between binary64 flushes
+
+__host__ __device__ inline int pk(int j, int n) { return j * n - (j * (j + 1)) / 2; }
+__host__ __device__ inline size_t up16(size_t b) { return (b + 15) / 16 * 16; }
+
+struct PipeLayout {
+    size_t ring, gbuf, bars, flag, total;
+};
+
+__host__ __device__ inline PipeLayout pipe_layout(int n, int k)
+{
+    const int kp = (k + 3) & ~3;
+    PipeLayout p;
+    size_t off = up16(sizeof(float) * (size_t)(n * (n + 1) / 2));  // packed R
+    p.ring = off;
+    off += up16(sizeof(float) * (size_t)kD * n * kRS);
+    p.gbuf = off;
+    off += up16(sizeof(float) * (size_t)kD * kp * kL);
+    p.bars = off;
+    off += sizeof(uint64_t) * 2 * kD * kMaxW;
+    p.flag = off;
+    off += 16;
+    p.total = off;
+    return p;
+}
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ uint64_t gtime()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* b)
+{
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+
+// Lane 0 waits for the phase of parity `par` to complete (bounded, and
+// abandoned at once when another warp has aborted); the outcome is
+// broadcast to the warp and ordered before the warp's later reads.
+__device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t par, volatile int* abort_flag, int* status)
+{
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) {
+        const uint32_t a = saddr(b);
+        const uint64_t t0 = gtime();
+        for (;;) {
+            uint32_t done;
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+                " selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(a), "r"(par)
+                : "memory");
+            if (done) break;
+            if (*abort_flag) {
+                ok = false;
+                break;
+            }
+            if (gtime() - t0 > 1000000000ull) {
+                *abort_flag = 1;
+                set_status(status, MRNMF_ERR_TIMEOUT);
+                ok = false;
+                break;
+            }
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok;
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(kMaxW * 32, 1) tsqr_pipe_kernel(const LeafArgs a)
+{
+    constexpr bool GP = KMAX > 0;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const unsigned FULL = 0xffffffffu;
+    const int n = a.n;
+    const int k = GP ? a.k : 0;
+    const int kp = (k + 3) & ~3;
+    const int W = (n + 31) / 32;
+    const int c = threadIdx.x, lane = c & 31, w = c >> 5;
+    const bool own = c < n;
+    const int jb0 = 32 * w, jb1 = min(32 * w + 32, n);  // this warp's block
+    const PipeLayout lay = pipe_layout(n, k);
+    float* Rs = reinterpret_cast<float*>(smem);
+    float* ring = reinterpret_cast<float*>(smem + lay.ring);
+    float* gbuf = reinterpret_cast<float*>(smem + lay.gbuf);
+    uint64_t* pub = reinterpret_cast<uint64_t*>(smem + lay.bars);  // [kD][kMaxW]
+    uint64_t* fre = pub + kD * kMaxW;                               // [kD][kMaxW]
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + lay.flag);
+    const int cta = blockIdx.x;
+
+    {
+        const float* Rin = static_cast<const float*>(a.R_in);
+        const int nn = n * n;
+        for (int e = c; e < nn; e += blockDim.x) {
+            const int j = e / n, cc = e - j * n;
+            if (cc >= j) Rs[pk(j, n) + cc] = Rin ? Rin[(size_t)cta * nn + e] : 0.f;
+        }
+    }
+    if (c == 0) {
+        for (int s = 0; s < kD; ++s)
+            for (int b = 0; b < kMaxW; ++b) {
+                bar_init(&pub[s * kMaxW + b], 1);
+                bar_init(&fre[s * kMaxW + b], (uint32_t)max(W - 1 - b, 1));
+            }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const int64_t r0 = (int64_t)cta * a.rows_per_cta;
+    const int64_t r1 = min(a.rows, r0 + a.rows_per_cta);
+    const int64_t ntiles = r1 > r0 ? (r1 - r0 + kL - 1) / kL : 0;
+    const float* X = static_cast<const float*>(a.X);
+
+    float av[kL];
+    float gacc[KMAX > 0 ? KMAX : 1];
+#pragma unroll
+    for (int q = 0; q < (KMAX > 0 ? KMAX : 1); ++q) gacc[q] = 0.f;
+    float cs_acc = 0.f;
+    bool bad = false;
+
+    // G' A(:, c) for this tile (original values of the column)
+    auto project = [&](const float* gs) {
+#pragma unroll
+        for (int q = 0; q < (KMAX > 0 ? KMAX : 1); ++q) {
+            if (q < k) {
+                const float4* gq = reinterpret_cast<const float4*>(gs + q * kL);
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int l4 = 0; l4 < kL / 4; ++l4) {
+                    const float4 g = gq[l4];
+                    s0 = fmaf(g.x, av[4 * l4], s0);
+                    s1 = fmaf(g.y, av[4 * l4 + 1], s1);
+                    s0 = fmaf(g.z, av[4 * l4 + 2], s0);
+                    s1 = fmaf(g.w, av[4 * l4 + 3], s1);
+                }
+                gacc[q] += s0 + s1;
+            }
+        }
+    };
+
+    int64_t t = 0;
+    for (; t < ntiles; ++t) {
+        const int s = (int)(t & (kD - 1));
+        const uint32_t par = (uint32_t)((t / kD) & 1);
+        const uint32_t par_prev = par ^ 1u;  // the slot's previous use (tile t - kD)
+        const int64_t row0 = r0 + t * kL;
+        const int rows_v = (int)min((int64_t)kL, r1 - row0);
+        float* rs = ring + (size_t)s * n * kRS;
+        float* gs = gbuf + (size_t)s * kp * kL;
+        {
+            const float* src = X + row0 * a.ldx + (own ? c : 0);
+#pragma unroll
+            for (int l = 0; l < kL; ++l) av[l] = (own && l < rows_v) ? __ldg(src + (int64_t)l * a.ldx) : 0.f;
+            float s0 = 0.f;
+#pragma unroll
+            for (int l = 0; l < kL; ++l) {
+                bad |= !(av[l] >= 0.f);
+                s0 += av[l];
+            }
+            cs_acc += s0;
+        }
+        bool ok = true;
+        if (w == 0) {
+            // the slot's G and block-0 reflectors of tile t - kD must be consumed
+            if (t >= kD && W > 1) ok = warp_wait(&fre[s * kMaxW + 0], par_prev, abort_flag, a.status);
+            if (!ok) break;
+            if (GP) {
+                const int kq = kp >> 2;
+                for (int idx = lane; idx < kL * kq; idx += 32) {
+                    const int l = idx / kq, q = idx - l * kq;
+                    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (l < rows_v) g = gauss4(a.seed, a.row_base + row0 + l, (uint32_t)q);
+                    gs[(4 * q + 0) * kL + l] = g.x;
+                    gs[(4 * q + 1) * kL + l] = g.y;
+                    gs[(4 * q + 2) * kL + l] = g.z;
+                    gs[(4 * q + 3) * kL + l] = g.w;
+                }
+                __syncwarp();
+                project(gs);
+            }
+        }
+        // the reflectors of the earlier blocks, in order
+        for (int b = 0; b < w && ok; ++b) {
+            ok = warp_wait(&pub[s * kMaxW + b], par, abort_flag, a.status);
+            if (!ok) break;
+            if (GP && b == 0) project(gs);
+            const int j1 = min(32 * b + 32, n);
+            for (int j = 32 * b; j < j1; ++j) {
+                const float* rv = rs + (size_t)j * kRS;
+                const float4* p4 = reinterpret_cast<const float4*>(rv);
+                float ga = 0.f, gb = 0.f, gc = 0.f, gd = 0.f;
+#pragma unroll
+                for (int l4 = 0; l4 < kL / 4; ++l4) {
+                    const float4 v = p4[l4];
+                    ga = fmaf(v.x, av[4 * l4], ga);
+                    gb = fmaf(v.y, av[4 * l4 + 1], gb);
+                    gc = fmaf(v.z, av[4 * l4 + 2], gc);
+                    gd = fmaf(v.w, av[4 * l4 + 3], gd);
+                }
+                const float g = (ga + gb) + (gc + gd);
+                const float d = rv[kL], rb = rv[kL + 1], rd = rv[kL + 2];
+                if (own) {
+                    const int e = pk(j, n) + c;
+                    const float r = Rs[e];
+                    const float wp = fmaf(d, r, g);
+                    const float f = (wp * rd) * rb;
+                    Rs[e] = fmaf(wp, rb, r);
+#pragma unroll
+                    for (int l4 = 0; l4 < kL / 4; ++l4) {
+                        const float4 v = p4[l4];
+                        av[4 * l4] = fmaf(f, v.x, av[4 * l4]);
+                        av[4 * l4 + 1] = fmaf(f, v.y, av[4 * l4 + 1]);
+                        av[4 * l4 + 2] = fmaf(f, v.z, av[4 * l4 + 2]);
+                        av[4 * l4 + 3] = fmaf(f, v.w, av[4 * l4 + 3]);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) bar_arrive(&fre[s * kMaxW + b]);
+        }
+        if (!ok) break;
+        // this warp's own column steps; its ring entries of tile t - kD must be consumed
+        if (w > 0 && t >= kD && w < W - 1) ok = warp_wait(&fre[s * kMaxW + w], par_prev, abort_flag, a.status);
+        if (!ok) break;
+        for (int j = jb0; j < jb1; ++j) {
+            float* rv = rs + (size_t)j * kRS;
+            if (c == j) {
+#pragma unroll
+                for (int l4 = 0; l4 < kL / 4; ++l4)
+                    reinterpret_cast<float4*>(rv)[l4] =
+                        make_float4(av[4 * l4], av[4 * l4 + 1], av[4 * l4 + 2], av[4 * l4 + 3]);
+            }
+            __syncwarp();
+            const float4* p4 = reinterpret_cast<const float4*>(rv);
+            float ga = 0.f, gb = 0.f, gc = 0.f, gd = 0.f;
+#pragma unroll
+            for (int l4 = 0; l4 < kL / 4; ++l4) {
+                const float4 v = p4[l4];
+                ga = fmaf(v.x, av[4 * l4], ga);
+                gb = fmaf(v.y, av[4 * l4 + 1], gb);
+                gc = fmaf(v.z, av[4 * l4 + 2], gc);
+                gd = fmaf(v.w, av[4 * l4 + 3], gd);
+            }
+            const float g = (ga + gb) + (gc + gd);
+            const float sig = __shfl_sync(FULL, g, j & 31);
+            const int pr = pk(j, n);
+            const float alpha = Rs[pr + j];
+            __syncwarp();
+            float beta = alpha, d = 0.f, rb = 0.f, rd = 0.f;
+            if (sig > 0.f) {
+                // beta = -sign(alpha) sqrt(alpha^2 + sigma); reciprocals of beta
+                // and d = alpha - beta, never of their product
+                const float nrm = sqrtf(fmaf(alpha, alpha, sig));
+                beta = alpha >= 0.f ? -nrm : nrm;
+                d = alpha - beta;
+                rb = __frcp_rn(beta);
+                rd = __frcp_rn(d);
+                if (own && c > j) {
+                    const float r = Rs[pr + c];
+                    const float wp = fmaf(d, r, g);
+                    const float f = (wp * rd) * rb;
+                    Rs[pr + c] = fmaf(wp, rb, r);
+#pragma unroll
+                    for (int l4 = 0; l4 < kL / 4; ++l4) {
+                        const float4 v = p4[l4];
+                        av[4 * l4] = fmaf(f, v.x, av[4 * l4]);
+                        av[4 * l4 + 1] = fmaf(f, v.y, av[4 * l4 + 1]);
+                        av[4 * l4 + 2] = fmaf(f, v.z, av[4 * l4 + 2]);
+                        av[4 * l4 + 3] = fmaf(f, v.w, av[4 * l4 + 3]);
+                    }
+                }
+            }
+            if (c == j) {
+                Rs[pr + j] = beta;
+                rv[kL] = d;  // d = rb = rd = 0 marks the identity (nothing below R_jj)
+                rv[kL + 1] = rb;
+                rv[kL + 2] = rd;
+            }
+            __syncwarp();
+        }
+        if (lane == 0 && w < W - 1) bar_arrive(&pub[s * kMaxW + w]);
+
+        if ((t + 1) % kFlushT == 0 || t + 1 == ntiles) {
+            if (own && a.cs) a.cs[(size_t)cta * n + c] += (double)cs_acc;
+            cs_acc = 0.f;
+            if (GP && a.gx && own) {
+#pragma unroll
+                for (int q = 0; q < (KMAX > 0 ? KMAX : 1); ++q)
+                    if (q < k) {
+                        a.gx[((size_t)cta * k + q) * n + c] += (double)gacc[q];
+                        gacc[q] = 0.f;
+                    }
+            }
+        }
+    }
+    if (a.check && __any_sync(FULL, bad) && lane == 0) set_status(a.status, MRNMF_ERR_BAD_INPUT);
+    __syncthreads();
+    float* Rout = static_cast<float*>(a.R_out) + (size_t)cta * n * n;
+    const int nn = n * n;
+    for (int e = c; e < nn; e += blockDim.x) {
+        const int j = e / n, cc = e - j * n;
+        Rout[e] = (cc >= j) ? Rs[pk(j, n) + cc] : 0.f;
+    }
+}
+
+template <int KMAX>
+cudaError_t launch_pipe_k(const LeafArgs& a, int grid, cudaStream_t s)
+{
+    const size_t smem = pipe_layout(a.n, KMAX > 0 ? a.k : 0).total;
+    auto kern = tsqr_pipe_kernel<KMAX>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (grid <= 0) return cudaSuccess;
+    kern<<<grid, ((a.n + 31) / 32) * 32, smem, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int KMAX>
+int pipe_ctas_per_sm_k(int n, int k)
+{
+    const size_t smem = pipe_layout(n, KMAX > 0 ? k : 0).total;
+    auto kern = tsqr_pipe_kernel<KMAX>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, ((n + 31) / 32) * 32, smem) != cudaSuccess)
+        return 1;
+    return blocks < 1 ? 1 : blocks;
+}
+
+}  // namespace
+
+bool pipe_leaf_supported(int n, int k)
+{
+    static const bool off = [] {
+        const char* v = getenv("MRNMF_PIPE_LEAF");
+        return v && v[0] == '0';
+    }();
+    return !off && n > 64 && n <= 256 && k >= 0 && k <= 64 && pipe_layout(n, k).total <= 220 * 1024;
+}
+
+int pipe_leaf_rows_per_tile() { return kL; }
+
+int pipe_leaf_ctas_per_sm(int n, int k)
+{
+    if (k <= 0) return pipe_ctas_per_sm_k<0>(n, 0);
+    if (k <= 16) return pipe_ctas_per_sm_k<16>(n, k);
+    if (k <= 32) return pipe_ctas_per_sm_k<32>(n, k);
+    if (k <= 48) return pipe_ctas_per_sm_k<48>(n, k);
+    return pipe_ctas_per_sm_k<64>(n, k);
+}
+
+cudaError_t launch_pipe_leaf(const LeafArgs& a, int grid, cudaStream_t s)
+{
+    const int k = (a.gx != nullptr && a.k > 0) ? a.k : 0;
+    if (k == 0) return launch_pipe_k<0>(a, grid, s);
+    if (k <= 16) return launch_pipe_k<16>(a, grid, s);
+    if (k <= 32) return launch_pipe_k<32>(a, grid, s);
+    if (k <= 48) return launch_pipe_k<48>(a, grid, s);
+    return launch_pipe_k<64>(a, grid, s);
+}
+
+}  // namespace mrnmf

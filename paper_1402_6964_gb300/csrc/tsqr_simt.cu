@@ -383,6 +383,15 @@ int choose_streams(int n, int k, int fp64, int tc, int64_t m)
         }
         return std::max(w, (P + w - 1) / w * w);
     }
+    if (!fp64 && pipe_leaf_supported(n, k)) {
+        int P = num_sms() * pipe_leaf_ctas_per_sm(n, k);
+        if (m > 0) {
+            const int64_t minrows = 4 * (int64_t)pipe_leaf_rows_per_tile();
+            const int64_t cap = std::max<int64_t>(1, (m + minrows - 1) / minrows);
+            P = (int)std::min<int64_t>(P, cap);
+        }
+        return std::max(P, 1);
+    }
     if (!fp64 && cta_leaf_supported(n, k)) {
         int P = num_sms() * std::min(8, cta_leaf_ctas_per_sm(n, k));
         if (m > 0) {
@@ -461,6 +470,11 @@ cudaError_t pass_push(PassState& st, const void* X, int64_t rows, int64_t ldx, i
         int64_t pw = (rows + st.P - 1) / st.P;
         a.rows_per_cta = ((pw + L - 1) / L) * L;
         e = launch_tc_leaf(a, st.P, s);
+    } else if (!st.fp64 && !xf64 && qr && pipe_leaf_supported(st.n, st.k)) {
+        const int L = pipe_leaf_rows_per_tile();
+        int64_t pw = (rows + st.P - 1) / st.P;
+        a.rows_per_cta = ((pw + L - 1) / L) * L;
+        e = launch_pipe_leaf(a, st.P, s);
     } else if (!st.fp64 && !xf64 && qr && cta_leaf_supported(st.n, st.k)) {
         const int L = cta_leaf_rows_per_tile(a.gx ? st.k : 0, st.n);
         int64_t pw = (rows + st.P - 1) / st.P;
