@@ -355,9 +355,22 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     w = synth.WORKLOADS[args.workload]
-    X, P = synth.workload_matrix(w, m=args.rows)
-    m, n, r, k = X.shape[0], w.n, w.r, w.k
-    Xd = torch.from_numpy(X).cuda()
+    m_req = args.rows or w.m
+    big = m_req * w.n * 4 > 16e9  # too large to draw on the host: draw it on the device
+    if big:
+        P = synth.planted_structure(w.n, w.r, w.seed, w.alpha, w.decades)
+        Xd = torch.empty((m_req, w.n), dtype=torch.float32, device="cuda")
+        ch = 1 << 23
+        for c0 in range(0, m_req, ch):
+            rows = min(ch, m_req - c0)
+            synth.device_planted(rows, w.n, w.r, w.seed, noise=w.noise, alpha=w.alpha, w_dist=w.w_dist,
+                                 chunk=c0 // ch, P=P, out=Xd[c0:c0 + rows])
+        torch.cuda.synchronize()
+        X = None
+    else:
+        X, P = synth.workload_matrix(w, m=args.rows)
+        Xd = torch.from_numpy(X).cuda()
+    m, n, r, k = Xd.shape[0], w.n, w.r, w.k
     dev = Xd.device
     h = mrnmf.Handle()
     stream = torch.cuda.current_stream()
@@ -440,22 +453,38 @@ def run_ours(args):
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"}
     roofline = roof_hbm if roof_hbm["frac"] >= roof_alu["frac"] else roof_alu
 
-    # R error of this pass vs the unique R (Cholesky of the FP64 Gram, host)
+    # R error of this pass vs the unique R (Cholesky of the binary64 Gram X'X,
+    # accumulated in row chunks on the device for device-drawn X)
     Rg = R.cpu().numpy()
-    G = X.astype(np.float64)
-    Gram = G.T @ G
-    del G
+    if big:
+        Gd = torch.zeros((n, n), dtype=torch.float64, device=dev)
+        for c0 in range(0, m, 1 << 20):
+            Xc = Xd[c0:c0 + (1 << 20)].double()
+            Gd += Xc.T @ Xc
+            del Xc
+        Gram = Gd.cpu().numpy()
+        del Gd
+    else:
+        G = X.astype(np.float64)
+        Gram = G.T @ G
+        del G
     r_err = {"gram_identity": float(np.linalg.norm(Rg.T @ Rg - Gram) / np.linalg.norm(Gram))}
-    try:
-        Rc = np.linalg.cholesky(Gram).T
-        r_err["rel_fro_vs_chol_gram"] = float(np.linalg.norm(Rg - Rc) / np.linalg.norm(Rc))
-    except np.linalg.LinAlgError:
-        pass  # Gram not numerically positive definite (ill-conditioned X): identity only
+    # chol(X'X)' is a usable reference only while cond(X'X) is far below
+    # 1/eps(binary64); beyond that (the ill-conditioned workload) the Gram
+    # identity alone is reported
+    cond_gram = float(np.linalg.cond(Gram))
+    r_err["cond_gram"] = cond_gram
+    if cond_gram < 1e10:
+        try:
+            Rc = np.linalg.cholesky(Gram).T
+            r_err["rel_fro_vs_chol_gram"] = float(np.linalg.norm(Rg - Rc) / np.linalg.norm(Rc))
+        except np.linalg.LinAlgError:
+            pass
     K_spa = sorted(Ks["spa"][0].cpu().numpy().tolist())
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not big:
         Xp = torch.from_numpy(X).pin_memory()
         h.factorize_host(Xp, r, method="spa", k=0, seed=w.seed, prec=args.prec)  # warm-up
         ne = max(1, min(args.steps, 5))
@@ -471,7 +500,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rows = args.cpu_rows
-        tcpu = cpu_oracle_step(X, w, rows)
+        Xh = X if X is not None else Xd[:rows].cpu().numpy()
+        tcpu = cpu_oracle_step(Xh, w, rows)
         cpu = {"value": 4.0 * rows * n / tcpu / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"first {rows} rows of the workload (pass + SPA/XRAY/GP + NNLS + residual), "
                          f"{tcpu:.1f} s"}

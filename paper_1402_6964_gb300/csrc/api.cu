@@ -5,6 +5,7 @@
 // step kernels (small_step.cu).  No entry point computes on the host.
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -386,9 +387,14 @@ mrnmf_status mrnmf_factorize_host(mrnmf_handle* h, const float* X, int64_t m, in
                 return cuda_fail(h, e, "events");
         }
     }
-    // two staging buffers of up to 64 MiB each
+    // two staging buffers of up to MRNMF_STAGE_MB MiB each (default 64)
+    static const int64_t stage_mb = [] {
+        const char* v = getenv("MRNMF_STAGE_MB");
+        const long x = v ? atol(v) : 64;
+        return (int64_t)(x >= 1 && x <= 4096 ? x : 64);
+    }();
     const int64_t row_bytes = (int64_t)n * 4;
-    int64_t chunk = std::max<int64_t>(1, (64ll << 20) / row_bytes);
+    int64_t chunk = std::max<int64_t>(1, (stage_mb << 20) / row_bytes);
     if (chunk > m) chunk = m;
     if ((s = grow(h, &h->xbuf, &h->xbuf_bytes, 2 * (size_t)chunk * row_bytes, "staging buffers")) != MRNMF_OK)
         return s;
