@@ -159,7 +159,8 @@ def test_gauss_project_row_offset(h, oracle):
     assert np.all(np.abs(host(GX) - GXo) <= 2e-6 * _gx_bound(X, 6, 42, 10_000_000_000) + 1e-12)
 
 
-@pytest.mark.parametrize("m,n,k", [(20011, 30, 12), (9001, 50, 20), (20011, 100, 40), (4003, 200, 40)])
+@pytest.mark.parametrize("m,n,k", [(20011, 30, 12), (9001, 50, 20), (20011, 100, 40), (4003, 200, 40),
+                                   (2000, 65, 17), (5000, 100, 64), (3001, 256, 64), (777, 224, 1)])
 def test_fused_pass_matches_separate(h, oracle, m, n, k):
     # Sec. 3.5: TSQR and GP in one pass give what the two separate passes give
     X = synth.random_nonneg(m, n, seed=3 + n)

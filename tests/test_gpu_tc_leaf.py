@@ -68,7 +68,7 @@ def test_tsqr_tf32x3_matches_oracle(h, oracle, m, n):
 
 
 @pytest.mark.parametrize("m,n,k", [(20011, 30, 12), (9001, 50, 20), (4099, 64, 31), (50000, 40, 1), (777, 18, 15),
-                                   (4096, 36, 16)])
+                                   (4096, 36, 16), (3000, 40, 32)])
 def test_fused_tf32x3_matches_oracle(h, oracle, m, n, k):
     X = synth.random_nonneg(m, n, seed=3 + n + k)
     R, cs, GX = h.tsqr_gp(dev(X), k, seed=99, prec="tf32x3")
