@@ -195,10 +195,15 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
     const bool om = NC == 2 ? true : own0;
     for (; j < n; ++j) {
         const float4* pj = reinterpret_cast<const float4*>(pub + (j & 1) * L);
+        // short tiles keep the pivot in registers for the update (one read of
+        // the publication buffer per step instead of two)
+        constexpr bool kPivReg = L <= 64;
+        float4 pv[kPivReg ? L / 4 : 1];
         float g0a = 0.f, g0b = 0.f, g0c = 0.f, g0d = 0.f;
 #pragma unroll
         for (int l4 = 0; l4 < L / 4; ++l4) {
             const float4 v = pj[l4];
+            if (kPivReg) pv[kPivReg ? l4 : 0] = v;
             g0a = fmaf(v.x, a0[4 * l4], g0a);
             g0b = fmaf(v.y, a0[4 * l4 + 1], g0b);
             g0c = fmaf(v.z, a0[4 * l4 + 2], g0c);
@@ -224,7 +229,7 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
             }
 #pragma unroll
             for (int l4 = 0; l4 < L / 4; ++l4) {
-                const float4 v = pj[l4];
+                const float4 v = kPivReg ? pv[kPivReg ? l4 : 0] : pj[l4];
                 a0[4 * l4] = fmaf(f0, v.x, a0[4 * l4]);
                 a0[4 * l4 + 1] = fmaf(f0, v.y, a0[4 * l4 + 1]);
                 a0[4 * l4 + 2] = fmaf(f0, v.z, a0[4 * l4 + 2]);
