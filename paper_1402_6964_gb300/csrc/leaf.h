@@ -49,11 +49,11 @@ struct TreeCta {
 
 // Warp-per-stream leaf (tsqr_warp.cu): binary32, n <= 64.  Streams = grid * warps_per_cta().
 bool warp_leaf_supported(int n, int k);
-int warp_leaf_rows_per_tile(int n);
+int warp_leaf_rows_per_tile(int n, int k);
 int warp_leaf_warps_per_cta();
 int warp_leaf_ctas_per_sm(int n, int k);
 cudaError_t launch_warp_leaf(const LeafArgs& a, int streams, cudaStream_t s);
-// family 1: n <= 32 (128-row tiles), family 2: 33 <= n <= 64 (32-row tiles)
+// family 1: n <= 32 (64-row tiles), family 2: 33 <= n <= 64 (32-row tiles)
 cudaError_t launch_warp_batched(const BatchCta* desc, int nctas, const BatchProblem* probs, int family, int max_n,
                                 int* status, cudaStream_t s);
 int warp_batched_rows_per_tile(int family);

@@ -377,7 +377,7 @@ int choose_streams(int n, int k, int fp64, int tc, int64_t m)
         const int w = warp_leaf_warps_per_cta();
         int P = num_sms() * warp_leaf_ctas_per_sm(n, k) * w;
         if (m > 0) {
-            const int64_t minrows = 2 * (int64_t)warp_leaf_rows_per_tile(n);
+            const int64_t minrows = 2 * (int64_t)warp_leaf_rows_per_tile(n, k);
             const int64_t cap = std::max<int64_t>(1, (m + minrows - 1) / minrows);
             P = (int)std::min<int64_t>(P, cap);
         }
@@ -481,7 +481,7 @@ cudaError_t pass_push(PassState& st, const void* X, int64_t rows, int64_t ldx, i
         a.rows_per_cta = ((pw + L - 1) / L) * L;
         e = launch_cta_leaf(a, st.P, s);
     } else if (warp_path) {
-        const int L = warp_leaf_rows_per_tile(st.n);
+        const int L = warp_leaf_rows_per_tile(st.n, a.gx ? st.k : 0);
         int64_t pw = (rows + st.P - 1) / st.P;
         a.rows_per_cta = ((pw + L - 1) / L) * L;
         e = launch_warp_leaf(a, st.P, s);

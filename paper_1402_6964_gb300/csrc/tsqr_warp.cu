@@ -898,6 +898,21 @@ int ctas_per_sm_nc(int n, int k)
 }
 
 // Tile height of the two-column form (32, or 64 when MRNMF_WARP_ROWS=64).
+// Tile height of the one-column form (n <= 32).  Measured on GB300 (4e7
+// rows): 64-row tiles are ~20% faster without the projection at every n
+// and with it from n ~ 29 on; 128-row tiles are ~12% faster with the
+// projection below that.  MRNMF_WARP_ROWS1=64|128 forces one height.
+int rows1(int n, int k)
+{
+    static int forced = [] {
+        const char* e = getenv("MRNMF_WARP_ROWS1");
+        const int v = e ? atoi(e) : 0;
+        return (v == 64 || v == 128) ? v : 0;
+    }();
+    if (forced) return forced;
+    return (k <= 0 || n > 28) ? 64 : 128;
+}
+
 int rows2()
 {
     static int v = [] {
@@ -920,18 +935,19 @@ cudaError_t tree_wide_level(const float* Rin, int P_in, int n, float* Rout, cuda
 bool warp_leaf_supported(int n, int k)
 {
     if (n < 1 || n > 64 || k > 64) return false;
-    const size_t smem = (size_t)kWarps * (n <= 32 ? warp_slice_bytes<128>(n, k)
+    const size_t smem = (size_t)kWarps * (n <= 32 ? (rows1(n, k) == 128 ? warp_slice_bytes<128>(n, k) : warp_slice_bytes<64>(n, k))
                                                   : (rows2() == 32 ? warp_slice_bytes<32>(n, k)
                                                                    : warp_slice_bytes<64>(n, k)));
     return smem <= 220 * 1024;
 }
 
-int warp_leaf_rows_per_tile(int n) { return n <= 32 ? 128 : rows2(); }
+int warp_leaf_rows_per_tile(int n, int k) { return n <= 32 ? rows1(n, k) : rows2(); }
 
 int warp_leaf_warps_per_cta() { return kWarps; }
 
 int warp_leaf_ctas_per_sm(int n, int k)
 {
+    if (n <= 32 && rows1(n, k) == 64) return k > 0 ? ctas_per_sm_nc<1, 64, true>(n, k) : ctas_per_sm_nc<1, 64, false>(n, k);
     if (n <= 32) return k > 0 ? ctas_per_sm_nc<1, 128, true>(n, k) : ctas_per_sm_nc<1, 128, false>(n, k);
     if (rows2() == 32) return k > 0 ? ctas_per_sm_nc<2, 32, true>(n, k) : ctas_per_sm_nc<2, 32, false>(n, k);
     return k > 0 ? ctas_per_sm_nc<2, 64, true>(n, k) : ctas_per_sm_nc<2, 64, false>(n, k);
@@ -944,11 +960,11 @@ cudaError_t launch_warp_batched(const BatchCta* desc, int nctas, const BatchProb
     cudaError_t e;
     size_t smem;
     if (family == 1) {
-        smem = (size_t)kWarps * warp_slice_bytes<128>(max_n, 0);
-        e = cudaFuncSetAttribute(tsqr_warp_batched_kernel<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        smem = (size_t)kWarps * warp_slice_bytes<64>(max_n, 0);
+        e = cudaFuncSetAttribute(tsqr_warp_batched_kernel<1, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        tsqr_warp_batched_kernel<1, 128><<<nctas, kWarps * 32, smem, s>>>(desc, probs, status);
+        tsqr_warp_batched_kernel<1, 64><<<nctas, kWarps * 32, smem, s>>>(desc, probs, status);
     } else {
         smem = (size_t)kWarps * warp_slice_bytes<32>(max_n, 0);
         e = cudaFuncSetAttribute(tsqr_warp_batched_kernel<2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -960,7 +976,7 @@ cudaError_t launch_warp_batched(const BatchCta* desc, int nctas, const BatchProb
     return cudaGetLastError();
 }
 
-int warp_batched_rows_per_tile(int family) { return family == 1 ? 128 : 32; }
+int warp_batched_rows_per_tile(int family) { return family == 1 ? 64 : 32; }
 
 bool cta_leaf_supported(int n, int k)
 {
@@ -1002,6 +1018,8 @@ cudaError_t launch_tree_batched(const TreeCta* desc, int nctas, int family, cuda
 cudaError_t launch_warp_leaf(const LeafArgs& a, int streams, cudaStream_t s)
 {
     const bool gp = a.gx != nullptr && a.k > 0;
+    if (a.n <= 32 && rows1(a.n, gp ? a.k : 0) == 64)
+        return gp ? launch_nc<1, 64, true>(a, streams, s) : launch_nc<1, 64, false>(a, streams, s);
     if (a.n <= 32) return gp ? launch_nc<1, 128, true>(a, streams, s) : launch_nc<1, 128, false>(a, streams, s);
     if (rows2() == 32) return gp ? launch_nc<2, 32, true>(a, streams, s) : launch_nc<2, 32, false>(a, streams, s);
     return gp ? launch_nc<2, 64, true>(a, streams, s) : launch_nc<2, 64, false>(a, streams, s);
