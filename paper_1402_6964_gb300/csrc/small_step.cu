@@ -356,10 +356,16 @@ __device__ __forceinline__ double rsqrt_d(double d)
     return y;
 }
 
+// r0 > 0: warm start from H's first r0 rows (a feasible point, x >= 0, of the
+// same problem with fewer columns -- greedy XRAY's previous pick).  The
+// passive set starts as its support; feasibility is restored on it by the
+// Lawson-Hanson inner loop before the usual outer iterations, so the result
+// is the same minimiser (unique when R(:,K) has full column rank).  H is read
+// and then overwritten, column by column (one warp per column).
 __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restrict__ AtA_g,
                                                            const double* __restrict__ Atb,
                                                            const double* __restrict__ btb, int r, int n,
-                                                           double* __restrict__ H, int* status)
+                                                           double* __restrict__ H, int r0, int* status)
 {
     __shared__ double AtA[32 * 32];
     for (int e = threadIdx.x; e < r * r; e += blockDim.x) AtA[e] = AtA_g[e];
@@ -486,42 +492,15 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
         return true;
     };
 
-    bool fact_ok = true;  // the factor covers exactly the passive set
-    for (int outer = 0;; ++outer) {
-        // dual w = A^T b - A^T A x
-        double w = rhs;
-        for (int q = 0; q < r; ++q) {
-            const double xq = shfl_d(x, q);
-            if (act) w -= AtA[lane * r + q] * xq;
-        }
-        // entering index: the largest dual above tol among non-passive (lowest index on ties)
-        double best = (act && !passive && w > tol) ? w : -1.0;
-        int bi = lane;
-        for (int o = 16; o; o >>= 1) {
-            const double ob = __shfl_xor_sync(FULL, best, o);
-            const int oi = __shfl_xor_sync(FULL, bi, o);
-            if (ob > best || (ob == best && oi < bi)) {
-                best = ob;
-                bi = oi;
-            }
-        }
-        if (best <= 0.0) break;  // KKT satisfied (no dual above tol)
-        if (outer >= 3 * r) {
-            st = MRNMF_ERR_NOT_CONVERGED;
-            break;
-        }
-        if (lane == bi) passive = true;
-        if (!__all_sync(FULL, fact_ok ? add_index(bi) : refactor())) {
-            st = MRNMF_ERR_RANK_DEFICIENT;
-            break;
-        }
-        fact_ok = true;
-        for (int inner = 0; inner <= r + 1; ++inner) {
+    // Lawson-Hanson inner loop: solve on the passive set, step back to the
+    // feasible boundary while a coefficient would be nonpositive
+    auto inner = [&]() {
+        for (int it = 0; it <= r + 1; ++it) {
             const bool in = lane < p;
             // forward solve L y = rhs[idx]
             const double bk = shfl_d(rhs, idx);  // lane k: rhs of its passive index (lanes >= p: junk, unused)
             double acc = 0.0, y = 0.0;
-#pragma unroll
+    #pragma unroll
             for (int k = 0; k < 32; ++k) {
                 if (k >= p) break;
                 double yk = 0.0;
@@ -535,7 +514,7 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
             // backward solve L^T z = y: z_k = (y_k - sum_{a>k} L(a,k) z_a) / L(k,k)
             double z = 0.0;
             double acc2 = 0.0;
-#pragma unroll
+    #pragma unroll
             for (int k = 31; k >= 0; --k) {
                 if (k >= p) continue;
                 double zk = 0.0;
@@ -577,7 +556,7 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
                 passive = false;
                 x = 0.0;
             }
-            if (inner == r + 1) {
+            if (it == r + 1) {
                 st = MRNMF_ERR_NOT_CONVERGED;
                 break;
             }
@@ -587,6 +566,50 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
                 break;
             }
         }
+    };
+
+    if (r0 > 0) {
+        if (act && lane < r0) {
+            const double v = H[(size_t)lane * n + c];
+            x = v > 0.0 ? v : 0.0;
+        }
+        passive = act && x > 0.0;
+        if (__any_sync(FULL, passive)) {
+            if (!__all_sync(FULL, refactor())) st = MRNMF_ERR_RANK_DEFICIENT;
+            else inner();
+        }
+    }
+    bool fact_ok = true;  // the factor covers exactly the passive set
+    for (int outer = 0; !st; ++outer) {
+        // dual w = A^T b - A^T A x
+        double w = rhs;
+        for (int q = 0; q < r; ++q) {
+            const double xq = shfl_d(x, q);
+            if (act) w -= AtA[lane * r + q] * xq;
+        }
+        // entering index: the largest dual above tol among non-passive (lowest index on ties)
+        double best = (act && !passive && w > tol) ? w : -1.0;
+        int bi = lane;
+        for (int o = 16; o; o >>= 1) {
+            const double ob = __shfl_xor_sync(FULL, best, o);
+            const int oi = __shfl_xor_sync(FULL, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if (best <= 0.0) break;  // KKT satisfied (no dual above tol)
+        if (outer >= 3 * r) {
+            st = MRNMF_ERR_NOT_CONVERGED;
+            break;
+        }
+        if (lane == bi) passive = true;
+        if (!__all_sync(FULL, fact_ok ? add_index(bi) : refactor())) {
+            st = MRNMF_ERR_RANK_DEFICIENT;
+            break;
+        }
+        fact_ok = true;
+        inner();
         if (st) break;
     }
     if (st && lane == 0) set_status(status, st);
@@ -877,14 +900,15 @@ SmallWs carve(void* ws, int n, int r)
     return w;
 }
 
+// r0 > 0 (r <= 32 only): H's first r0 rows hold a warm start (see nnls_lh_warp_kernel).
 cudaError_t nnls_core(const double* R, int n, const int32_t* K, int r, double* H, const SmallWs& w, int* status,
-                      cudaStream_t s)
+                      cudaStream_t s, int r0 = 0)
 {
     const int total = r * r + r * n + n;
     nnls_gram_kernel<<<(total + 127) / 128, 128, 0, s>>>(R, n, K, r, w.AtA, w.Atb, w.btb);
     count_launch();
     if (r <= 32) {
-        nnls_lh_warp_kernel<<<(n + 3) / 4, 128, 0, s>>>(w.AtA, w.Atb, w.btb, r, n, H, status);
+        nnls_lh_warp_kernel<<<(n + 3) / 4, 128, 0, s>>>(w.AtA, w.Atb, w.btb, r, n, H, r0, status);
         count_launch();
         return cudaGetLastError();
     }
@@ -943,7 +967,8 @@ cudaError_t select_xray(const double* R, int n, int r, int32_t* K, double* gap, 
         count_launch();
         xray_pick_kernel<<<1, 256, 0, s>>>(w.score, n, t, w.chosen, K, gap, w.s0);
         count_launch();
-        cudaError_t e = nnls_core(R, n, K, t + 1, w.Hs, w, status, s);
+        // warm start from the previous pick's coefficients (same K prefix)
+        cudaError_t e = nnls_core(R, n, K, t + 1, w.Hs, w, status, s, t);
         if (e != cudaSuccess) return e;
         xray_res_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(R, n, K, t + 1, w.Hs, w.Y);
         count_launch();
