@@ -78,7 +78,7 @@ int tc_leaf_ctas_per_sm();
 cudaError_t launch_tc_leaf(const LeafArgs& a, int grid, cudaStream_t s);  // triangles folded per tree CTA
 cudaError_t launch_tree_batched(const TreeCta* desc, int nctas, int family, cudaStream_t s);
 
-// Wide tree level (binary32, n <= 64): P_in triangles -> *P_out = ceil(P_in / (S+1)).
+// Wide tree level (binary32, n <= 128): P_in triangles -> *P_out = ceil(P_in / (S+1)).
 bool wide_tree_supported(int n);
 cudaError_t tree_wide_level(const float* Rin, int P_in, int n, float* Rout, cudaStream_t s, int* P_out);
 

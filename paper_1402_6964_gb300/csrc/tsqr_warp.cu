@@ -924,12 +924,13 @@ int rows2()
 
 }  // namespace
 
-bool wide_tree_supported(int n) { return n >= 1 && n <= 64; }
+bool wide_tree_supported(int n) { return n >= 1 && n <= 128; }
 
 cudaError_t tree_wide_level(const float* Rin, int P_in, int n, float* Rout, cudaStream_t s, int* P_out)
 {
     if (n <= 32) return launch_tree_wide<32, 16>(Rin, P_in, n, Rout, s, P_out);
-    return launch_tree_wide<64, 8>(Rin, P_in, n, Rout, s, P_out);
+    if (n <= 64) return launch_tree_wide<64, 8>(Rin, P_in, n, Rout, s, P_out);
+    return launch_tree_wide<128, 3>(Rin, P_in, n, Rout, s, P_out);
 }
 
 bool warp_leaf_supported(int n, int k)
