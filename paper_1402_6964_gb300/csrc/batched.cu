@@ -1,12 +1,13 @@
 // batched.cu -- many independent tall-and-skinny problems (uneven m and n) in
 // one pass: mrnmf_tsqr_r_batched.
 //
-// Problems with n <= 64 go through the warp-per-stream leaf in one launch per
-// family (n <= 32 with 128-row tiles; 33..64 with 32-row tiles), each CTA
-// reading its problem from a descriptor table; then one launch per tree level
-// per family folds each problem's CTA triangles (fan-in 17 or 9), and one
-// launch writes every R and colsum.  Problems with n > 64 run the one-problem
-// pass in turn on the same stream.
+// Problems with n <= 128 go through one leaf launch per family, each CTA
+// reading its problem from a descriptor table: the warp-per-stream leaf for
+// n <= 32 (64-row tiles) and 33..64 (32-row tiles, four streams per CTA), the
+// warp-pipelined leaf for 65..128 (one stream per CTA).  Then one launch per
+// tree level per family folds each problem's triangles (fan-in 17, 9 or 4),
+// and one launch writes every R and colsum.  Problems with n > 128 run the
+// one-problem pass in turn on the same stream.
 //
 // Planning (the host side, done per call): each problem gets a share of the
 // family's streams proportional to its estimated cost m * n * (issue cost per
@@ -17,6 +18,7 @@
 // handle's buffers are large enough, so a warmed-up call can be captured in a
 // CUDA graph and replayed.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <tuple>
@@ -64,10 +66,12 @@ __global__ void __launch_bounds__(256) batched_finalize_kernel(const FinalDesc* 
 
 size_t al16(size_t b) { return (b + 15) & ~size_t(15); }
 
+constexpr int kFam = 3;  // n <= 32 and 33..64 (warp leaf), 65..128 (warp-pipelined leaf)
+
 struct BatchPlan {
-    std::vector<BatchProblem> probs[2];
-    std::vector<BatchCta> ctas[2];
-    std::vector<std::vector<TreeCta>> levels[2];
+    std::vector<BatchProblem> probs[kFam];
+    std::vector<BatchCta> ctas[kFam];
+    std::vector<std::vector<TreeCta>> levels[kFam];
     std::vector<FinalDesc> finals;
     std::vector<int> big;  // problems left to the one-problem pass
 };
@@ -75,35 +79,55 @@ struct BatchPlan {
 // Build the plan with device pointers into `dev` (layout: descriptors, then
 // triangles, then partial sums); returns the bytes needed.  With dev == nullptr
 // only sizes are computed.
-size_t plan_batched(const mrnmf_problem* pr, int count, int sms, int ctas_per_sm[2], BatchPlan& plan,
+// Waves of resident CTAs the pipelined family's streams are planned for
+// (MRNMF_PIPE_WAVES, default 32): its CTAs run long dependent chains, so
+// many short streams balance the batch (measured on the 256-problem batch:
+// 2 waves 496 ms, 8 waves 413 ms, 32 waves 390 ms).
+const double kPipeWaves = [] {
+    const char* v = getenv("MRNMF_PIPE_WAVES");
+    const double x = v ? atof(v) : 32.0;
+    return x >= 1.0 && x <= 64.0 ? x : 32.0;
+}();
+
+// streams per CTA and tile height of family f
+int fam_spc(int f) { return f < 2 ? 4 : 1; }
+int fam_rows(int f) { return f < 2 ? warp_batched_rows_per_tile(f + 1) : pipe_leaf_rows_per_tile(); }
+double fam_cost(int f, const mrnmf_problem& q)
+{
+    const double mn = (double)q.m * q.n;
+    return f == 0 ? 2.5 * mn : (f == 1 ? 6.0 * mn : mn * q.n / 16.0);
+}
+
+size_t plan_batched(const mrnmf_problem* pr, int count, int sms, int ctas_per_sm[kFam], BatchPlan& plan,
                     unsigned char* dev, size_t* desc_bytes, size_t* cs_off, size_t* cs_bytes)
 {
     plan = BatchPlan();
     // split and cost
     std::vector<int> fam(count);
-    double cost[2] = {0.0, 0.0};
+    double cost[kFam] = {0.0, 0.0, 0.0};
     for (int i = 0; i < count; ++i) {
         const int n = pr[i].n;
-        fam[i] = n <= 32 ? 0 : (n <= 64 ? 1 : -1);
+        fam[i] = n <= 32 ? 0 : (n <= 64 ? 1 : ((n <= 128 && pipe_leaf_supported(n, 0)) ? 2 : -1));
         if (fam[i] < 0) {
             plan.big.push_back(i);
             continue;
         }
-        cost[fam[i]] += (double)pr[i].m * n * (fam[i] == 0 ? 2.5 : 6.0);
+        cost[fam[i]] += fam_cost(fam[i], pr[i]);
     }
-    // streams: two waves of the family's resident warps
+    // streams: two waves of the family's resident streams
     std::vector<int> streams(count, 0);
     std::vector<int64_t> rps(count, 0);
     for (int i = 0; i < count; ++i) {
         if (fam[i] < 0) continue;
         const int f = fam[i];
-        const int L = warp_batched_rows_per_tile(f + 1);
-        const double budget = 2.0 * sms * ctas_per_sm[f] * 4;
-        const double share = cost[f] > 0 ? (double)pr[i].m * pr[i].n * (f == 0 ? 2.5 : 6.0) / cost[f] : 1.0;
+        const int L = fam_rows(f), spc = fam_spc(f);
+        const double waves = f < 2 ? 2.0 : kPipeWaves;
+        const double budget = waves * sms * ctas_per_sm[f] * spc;
+        const double share = cost[f] > 0 ? fam_cost(f, pr[i]) / cost[f] : 1.0;
         int64_t s = (int64_t)(budget * share + 0.5);
         const int64_t tiles = (pr[i].m + L - 1) / L;
         s = std::min<int64_t>(s, tiles);
-        s = std::max<int64_t>(4, (s + 3) / 4 * 4);
+        s = std::max<int64_t>(spc, (s + spc - 1) / spc * spc);
         streams[i] = (int)s;
         int64_t per = (pr[i].m + s - 1) / s;
         rps[i] = (per + L - 1) / L * L;
@@ -114,23 +138,23 @@ size_t plan_batched(const mrnmf_problem* pr, int count, int sms, int ctas_per_sm
     for (int i = 0; i < count; ++i) {
         if (fam[i] < 0) continue;
         leaf_off[i] = tri_floats;
-        tri_floats += (size_t)(streams[i] / 4) * pr[i].n * pr[i].n;
+        tri_floats += (size_t)(streams[i] / fam_spc(fam[i])) * pr[i].n * pr[i].n;
     }
     // descriptor counts first (sizes only), then pointers once the layout is known
-    int nprob[2] = {0, 0}, nctas[2] = {0, 0};
+    int nprob[kFam] = {0, 0, 0}, nctas[kFam] = {0, 0, 0};
     for (int i = 0; i < count; ++i)
         if (fam[i] >= 0) {
             nprob[fam[i]]++;
-            nctas[fam[i]] += streams[i] / 4;
+            nctas[fam[i]] += streams[i] / fam_spc(fam[i]);
         }
     // tree levels: (problem, input offset, count, output offset) per tree CTA
     std::vector<size_t> final_off(count, 0);
-    std::vector<std::vector<std::tuple<int, size_t, int, size_t>>> lv_raw[2];
+    std::vector<std::vector<std::tuple<int, size_t, int, size_t>>> lv_raw[kFam];
     for (int i = 0; i < count; ++i) {
         if (fam[i] < 0) continue;
         const int f = fam[i], n = pr[i].n, F = tree_fan_in(f + 1);
         size_t in_off = leaf_off[i];
-        int c = streams[i] / 4;
+        int c = streams[i] / fam_spc(f);
         int level = 0;
         while (c > 1) {
             const int outs = (c + F - 1) / F;
@@ -149,11 +173,11 @@ size_t plan_batched(const mrnmf_problem* pr, int count, int sms, int ctas_per_sm
     }
     // descriptor area, in the order pack_plan writes it
     size_t off = 0;
-    for (int f = 0; f < 2; ++f) off = al16(off + sizeof(BatchProblem) * nprob[f]);
-    for (int f = 0; f < 2; ++f) off = al16(off + sizeof(BatchCta) * nctas[f]);
-    for (int f = 0; f < 2; ++f)
+    for (int f = 0; f < kFam; ++f) off = al16(off + sizeof(BatchProblem) * nprob[f]);
+    for (int f = 0; f < kFam; ++f) off = al16(off + sizeof(BatchCta) * nctas[f]);
+    for (int f = 0; f < kFam; ++f)
         for (auto& L : lv_raw[f]) off = al16(off + sizeof(TreeCta) * L.size());
-    off = al16(off + sizeof(FinalDesc) * (nprob[0] + nprob[1]));
+    off = al16(off + sizeof(FinalDesc) * (nprob[0] + nprob[1] + nprob[2]));
     *desc_bytes = off;
     const size_t tri_off = off;
     off = al16(off + sizeof(float) * tri_floats);
@@ -185,7 +209,7 @@ size_t plan_batched(const mrnmf_problem* pr, int count, int sms, int ctas_per_sm
         b.cs = csb + cs_at[i];
         pidx[i] = (int)plan.probs[f].size();
         plan.probs[f].push_back(b);
-        for (int c = 0; c < streams[i] / 4; ++c) plan.ctas[f].push_back(BatchCta{pidx[i], c});
+        for (int c = 0; c < streams[i] / fam_spc(f); ++c) plan.ctas[f].push_back(BatchCta{pidx[i], c});
         FinalDesc fd;
         fd.Rfin = tri + final_off[i];
         fd.n = pr[i].n;
@@ -195,7 +219,7 @@ size_t plan_batched(const mrnmf_problem* pr, int count, int sms, int ctas_per_sm
         fd.colsum = pr[i].colsum;
         plan.finals.push_back(fd);
     }
-    for (int f = 0; f < 2; ++f)
+    for (int f = 0; f < kFam; ++f)
         for (auto& L : lv_raw[f]) {
             std::vector<TreeCta> v;
             for (auto& e : L) {
@@ -210,9 +234,9 @@ size_t plan_batched(const mrnmf_problem* pr, int count, int sms, int ctas_per_sm
 // Serialise the plan's descriptors into `host` (desc_bytes long) in the layout
 // plan_batched computed; returns device pointers of each table.
 struct PlanPtrs {
-    const BatchProblem* probs[2];
-    const BatchCta* ctas[2];
-    std::vector<const TreeCta*> levels[2];
+    const BatchProblem* probs[kFam];
+    const BatchCta* ctas[kFam];
+    std::vector<const TreeCta*> levels[kFam];
     const FinalDesc* finals;
 };
 
@@ -226,28 +250,30 @@ PlanPtrs pack_plan(const BatchPlan& plan, unsigned char* host, unsigned char* de
         off = al16(off + bytes);
         return d;
     };
-    for (int f = 0; f < 2; ++f)
+    for (int f = 0; f < kFam; ++f)
         p.probs[f] = reinterpret_cast<const BatchProblem*>(
             put(plan.probs[f].data(), sizeof(BatchProblem) * plan.probs[f].size()));
-    for (int f = 0; f < 2; ++f)
+    for (int f = 0; f < kFam; ++f)
         p.ctas[f] = reinterpret_cast<const BatchCta*>(put(plan.ctas[f].data(), sizeof(BatchCta) * plan.ctas[f].size()));
-    for (int f = 0; f < 2; ++f)
+    for (int f = 0; f < kFam; ++f)
         for (auto& L : plan.levels[f])
             p.levels[f].push_back(reinterpret_cast<const TreeCta*>(put(L.data(), sizeof(TreeCta) * L.size())));
     p.finals = reinterpret_cast<const FinalDesc*>(put(plan.finals.data(), sizeof(FinalDesc) * plan.finals.size()));
     return p;
 }
 
-cudaError_t run_batched_plan(const BatchPlan& plan, const PlanPtrs& p, int max_n[2], int* status, cudaStream_t s)
+cudaError_t run_batched_plan(const BatchPlan& plan, const PlanPtrs& p, int max_n[kFam], int* status, cudaStream_t s)
 {
     cudaError_t e;
     for (int f = 0; f < 2; ++f) {
         e = launch_warp_batched(p.ctas[f], (int)plan.ctas[f].size(), p.probs[f], f + 1, max_n[f], status, s);
         if (e != cudaSuccess) return e;
     }
-    const size_t nlev = std::max(plan.levels[0].size(), plan.levels[1].size());
+    e = launch_pipe_batched(p.ctas[2], (int)plan.ctas[2].size(), p.probs[2], max_n[2], status, s);
+    if (e != cudaSuccess) return e;
+    const size_t nlev = std::max({plan.levels[0].size(), plan.levels[1].size(), plan.levels[2].size()});
     for (size_t l = 0; l < nlev; ++l)
-        for (int f = 0; f < 2; ++f)
+        for (int f = 0; f < kFam; ++f)
             if (l < plan.levels[f].size()) {
                 e = launch_tree_batched(p.levels[f][l], (int)plan.levels[f][l].size(), f + 1, s);
                 if (e != cudaSuccess) return e;
@@ -281,7 +307,14 @@ extern "C" mrnmf_status mrnmf_tsqr_r_batched(mrnmf_handle* h, const mrnmf_proble
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int ctas[2] = {mrnmf::warp_leaf_ctas_per_sm(32, 0), mrnmf::warp_leaf_ctas_per_sm(64, 0)};
+    int max_n[3] = {1, 1, 65};
+    for (int i = 0; i < count; ++i) {
+        if (pr[i].n <= 32) max_n[0] = std::max(max_n[0], (int)pr[i].n);
+        else if (pr[i].n <= 64) max_n[1] = std::max(max_n[1], (int)pr[i].n);
+        else if (pr[i].n <= 128) max_n[2] = std::max(max_n[2], (int)pr[i].n);
+    }
+    int ctas[3] = {mrnmf::warp_leaf_ctas_per_sm(32, 0), mrnmf::warp_leaf_ctas_per_sm(64, 0),
+                   mrnmf::pipe_leaf_ctas_per_sm(max_n[2], 0)};
     mrnmf::BatchPlan plan;
     size_t desc_bytes = 0, cs_off = 0, cs_bytes = 0;
     const size_t need = mrnmf::plan_batched(pr, count, sms, ctas, plan, nullptr, &desc_bytes, &cs_off, &cs_bytes);
@@ -314,11 +347,6 @@ extern "C" mrnmf_status mrnmf_tsqr_r_batched(mrnmf_handle* h, const mrnmf_proble
     if ((e = cudaEventRecord(h->ev_bstage, s)) != cudaSuccess) return cuda_fail(h, e, "event");
     if (cs_bytes && (e = cudaMemsetAsync(devb + cs_off, 0, cs_bytes, s)) != cudaSuccess)
         return cuda_fail(h, e, "partial sums");
-    int max_n[2] = {1, 1};
-    for (int i = 0; i < count; ++i) {
-        if (pr[i].n <= 32) max_n[0] = std::max(max_n[0], (int)pr[i].n);
-        else if (pr[i].n <= 64) max_n[1] = std::max(max_n[1], (int)pr[i].n);
-    }
     if ((e = mrnmf::run_batched_plan(plan, ptrs, max_n, h->d_status, s)) != cudaSuccess)
         return cuda_fail(h, e, "batched pass");
     for (int i : plan.big) {

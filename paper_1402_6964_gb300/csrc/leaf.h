@@ -37,7 +37,7 @@ struct BatchProblem {
 };
 struct BatchCta {
     int p;    // problem
-    int cta;  // CTA index within the problem (streams 4*cta .. 4*cta+3)
+    int cta;  // CTA index within the problem (warp families: streams 4*cta .. 4*cta+3; family 3: stream cta)
 };
 
 struct TreeCta {
@@ -71,6 +71,9 @@ bool pipe_leaf_supported(int n, int k);
 int pipe_leaf_rows_per_tile();
 int pipe_leaf_ctas_per_sm(int n, int k);
 cudaError_t launch_pipe_leaf(const LeafArgs& a, int grid, cudaStream_t s);
+// Batched form (batched.cu family 3): one stream per CTA, no projection.
+cudaError_t launch_pipe_batched(const BatchCta* desc, int nctas, const BatchProblem* probs, int max_n, int* status,
+                                cudaStream_t s);
 
 // Tensor-core leaf (tsqr_tc.cu): 16 < n <= 64, k <= 32; one stream per CTA.
 int tc_leaf_rows_per_tile();

@@ -117,8 +117,12 @@ __device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t par, volatile in
     return ok;
 }
 
+// One stream (row range cta * rows_per_cta ..) of the problem in `a`; the
+// block may have more warps than the problem's column blocks (batched
+// launches size the block for the widest problem): those warps only meet the
+// CTA-wide barriers.
 template <int KMAX>
-__global__ void __launch_bounds__(kMaxW * 32, 1) tsqr_pipe_kernel(const LeafArgs a)
+__device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
 {
     constexpr bool GP = KMAX > 0;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -137,7 +141,6 @@ __global__ void __launch_bounds__(kMaxW * 32, 1) tsqr_pipe_kernel(const LeafArgs
     uint64_t* pub = reinterpret_cast<uint64_t*>(smem + lay.bars);  // [kD][kMaxW]
     uint64_t* fre = pub + kD * kMaxW;                               // [kD][kMaxW]
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + lay.flag);
-    const int cta = blockIdx.x;
 
     {
         const float* Rin = static_cast<const float*>(a.R_in);
@@ -160,7 +163,7 @@ __global__ void __launch_bounds__(kMaxW * 32, 1) tsqr_pipe_kernel(const LeafArgs
 
     const int64_t r0 = (int64_t)cta * a.rows_per_cta;
     const int64_t r1 = min(a.rows, r0 + a.rows_per_cta);
-    const int64_t ntiles = r1 > r0 ? (r1 - r0 + kL - 1) / kL : 0;
+    const int64_t ntiles = (r1 > r0 && w < W) ? (r1 - r0 + kL - 1) / kL : 0;
     const float* X = static_cast<const float*>(a.X);
 
     float av[kL];
@@ -356,6 +359,38 @@ __global__ void __launch_bounds__(kMaxW * 32, 1) tsqr_pipe_kernel(const LeafArgs
 }
 
 template <int KMAX>
+__global__ void __launch_bounds__(kMaxW * 32, 1) tsqr_pipe_kernel(const LeafArgs a)
+{
+    pipe_body<KMAX>(a, blockIdx.x);
+}
+
+// Batched form: CTA b runs stream desc[b].cta of problem desc[b].p (R from
+// zero, no projection); triangles and partial column sums go to the
+// problem's slots.
+__global__ void __launch_bounds__(kMaxW * 32, 1) tsqr_pipe_batched_kernel(const BatchCta* __restrict__ desc,
+                                                                          const BatchProblem* __restrict__ probs,
+                                                                          int* status)
+{
+    const BatchCta d = desc[blockIdx.x];
+    const BatchProblem pb = probs[d.p];
+    LeafArgs a{};
+    a.X = pb.X;
+    a.rows = pb.m;
+    a.ldx = pb.ldx;
+    a.n = pb.n;
+    a.rows_per_cta = pb.rows_per_stream;
+    a.row_base = 0;
+    a.R_in = nullptr;
+    a.R_out = pb.tri;
+    a.cs = pb.cs;
+    a.gx = nullptr;
+    a.k = 0;
+    a.check = 1;
+    a.status = status;
+    pipe_body<0>(a, d.cta);
+}
+
+template <int KMAX>
 cudaError_t launch_pipe_k(const LeafArgs& a, int grid, cudaStream_t s)
 {
     const size_t smem = pipe_layout(a.n, KMAX > 0 ? a.k : 0).total;
@@ -401,6 +436,19 @@ int pipe_leaf_ctas_per_sm(int n, int k)
     if (k <= 32) return pipe_ctas_per_sm_k<32>(n, k);
     if (k <= 48) return pipe_ctas_per_sm_k<48>(n, k);
     return pipe_ctas_per_sm_k<64>(n, k);
+}
+
+cudaError_t launch_pipe_batched(const BatchCta* desc, int nctas, const BatchProblem* probs, int max_n, int* status,
+                                cudaStream_t s)
+{
+    if (nctas <= 0) return cudaSuccess;
+    const size_t smem = pipe_layout(max_n, 0).total;
+    cudaError_t e =
+        cudaFuncSetAttribute(tsqr_pipe_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    tsqr_pipe_batched_kernel<<<nctas, ((max_n + 31) / 32) * 32, smem, s>>>(desc, probs, status);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pipe_leaf(const LeafArgs& a, int grid, cudaStream_t s)

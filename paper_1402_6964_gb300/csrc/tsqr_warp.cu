@@ -1005,13 +1005,14 @@ cudaError_t launch_cta_leaf(const LeafArgs& a, int grid, cudaStream_t s)
     return launch_cta_k<64, 32>(a, grid, s);
 }
 
-int tree_fan_in(int family) { return family == 1 ? 17 : 9; }
+int tree_fan_in(int family) { return family == 1 ? 17 : (family == 2 ? 9 : 4); }
 
 cudaError_t launch_tree_batched(const TreeCta* desc, int nctas, int family, cudaStream_t s)
 {
     if (nctas <= 0) return cudaSuccess;
     if (family == 1) tsqr_tree_wide_batched_kernel<32, 16><<<nctas, 32 * 16, 0, s>>>(desc);
-    else tsqr_tree_wide_batched_kernel<64, 8><<<nctas, 64 * 8, 0, s>>>(desc);
+    else if (family == 2) tsqr_tree_wide_batched_kernel<64, 8><<<nctas, 64 * 8, 0, s>>>(desc);
+    else tsqr_tree_wide_batched_kernel<128, 3><<<nctas, 128 * 3, 0, s>>>(desc);
     count_launch();
     return cudaGetLastError();
 }
