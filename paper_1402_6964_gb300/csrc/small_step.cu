@@ -362,23 +362,38 @@ __device__ __forceinline__ double rsqrt_d(double d)
 // Lawson-Hanson inner loop before the usual outer iterations, so the result
 // is the same minimiser (unique when R(:,K) has full column rank).  H is read
 // and then overwritten, column by column (one warp per column).
-__global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restrict__ AtA_g,
-                                                           const double* __restrict__ Atb,
-                                                           const double* __restrict__ btb, int r, int n,
+// The normal equations are formed here (the same sums, in the same order, as
+// nnls_gram_kernel): A'A = R(:,K)'R(:,K) in shared memory per block, and per
+// column A'b = R(:,K)'R(:,c) and b'b = |R(:,c)|^2.
+__global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restrict__ R,
+                                                           const int32_t* __restrict__ K, int r, int n,
                                                            double* __restrict__ H, int r0, int* status)
 {
     __shared__ double AtA[32 * 32];
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) AtA[e] = AtA_g[e];
+    __shared__ int Ks[32];
+    for (int a = threadIdx.x; a < r; a += blockDim.x) Ks[a] = K[a];
+    __syncthreads();
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+        const int ca = Ks[e / r], cb = Ks[e % r];
+        double sum = 0.0;
+        for (int i = 0; i < n; ++i) sum += R[(size_t)i * n + ca] * R[(size_t)i * n + cb];
+        AtA[e] = sum;
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (c >= n) return;
     const unsigned FULL = 0xffffffffu;
     const bool act = lane < r;
-    const double rhs = act ? Atb[(size_t)lane * n + c] : 0.0;
+    double rhs = 0.0;
+    if (act) {
+        const int ca = Ks[lane];
+        for (int i = 0; i < n; ++i) rhs += R[(size_t)i * n + ca] * R[(size_t)i * n + c];
+    }
     double maxdiag = act ? AtA[lane * r + lane] : 0.0;
     for (int o = 16; o; o >>= 1) maxdiag = fmax(maxdiag, __shfl_xor_sync(FULL, maxdiag, o));
-    const double bb = btb[c];
+    double bb = 0.0;
+    for (int i = 0; i < n; ++i) bb += R[(size_t)i * n + c] * R[(size_t)i * n + c];
     const double tol = 1e-12 * sqrt(maxdiag * (bb > 0.0 ? bb : 0.0));
     double x = 0.0;
     bool passive = false;
@@ -904,14 +919,14 @@ SmallWs carve(void* ws, int n, int r)
 cudaError_t nnls_core(const double* R, int n, const int32_t* K, int r, double* H, const SmallWs& w, int* status,
                       cudaStream_t s, int r0 = 0)
 {
-    const int total = r * r + r * n + n;
-    nnls_gram_kernel<<<(total + 127) / 128, 128, 0, s>>>(R, n, K, r, w.AtA, w.Atb, w.btb);
-    count_launch();
     if (r <= 32) {
-        nnls_lh_warp_kernel<<<(n + 3) / 4, 128, 0, s>>>(w.AtA, w.Atb, w.btb, r, n, H, r0, status);
+        nnls_lh_warp_kernel<<<(n + 3) / 4, 128, 0, s>>>(R, K, r, n, H, r0, status);
         count_launch();
         return cudaGetLastError();
     }
+    const int total = r * r + r * n + n;
+    nnls_gram_kernel<<<(total + 127) / 128, 128, 0, s>>>(R, n, K, r, w.AtA, w.Atb, w.btb);
+    count_launch();
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
