@@ -131,9 +131,15 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
     const int k = GP ? a.k : 0;
     const int kp = (k + 3) & ~3;
     const int W = (n + 31) / 32;
-    const int c = threadIdx.x, lane = c & 31, w = c >> 5;
-    const bool own = c < n;
-    const int jb0 = 32 * w, jb1 = min(32 * w + 32, n);  // this warp's block
+    // Column blocks: the partial block (rem = n - 32 (W - 1) columns) first,
+    // then full 32-column blocks, so the warps that apply the most reflectors
+    // have every lane busy.  Block b = [bstart(b), bstart(b + 1)).
+    const int rem = n - 32 * (W - 1);
+    auto bstart = [&](int b) { return b == 0 ? 0 : rem + 32 * (b - 1); };
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int jb0 = w < W ? bstart(w) : n, jb1 = w < W ? bstart(w + 1) : n;  // this warp's block
+    const int c = jb0 + lane;                                                  // this thread's column
+    const bool own = c < jb1;
     const PipeLayout lay = pipe_layout(n, k);
     float* Rs = reinterpret_cast<float*>(smem);
     float* ring = reinterpret_cast<float*>(smem + lay.ring);
@@ -145,12 +151,12 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
     {
         const float* Rin = static_cast<const float*>(a.R_in);
         const int nn = n * n;
-        for (int e = c; e < nn; e += blockDim.x) {
+        for (int e = (int)threadIdx.x; e < nn; e += blockDim.x) {
             const int j = e / n, cc = e - j * n;
             if (cc >= j) Rs[pk(j, n) + cc] = Rin ? Rin[(size_t)cta * nn + e] : 0.f;
         }
     }
-    if (c == 0) {
+    if (threadIdx.x == 0) {
         for (int s = 0; s < kD; ++s)
             for (int b = 0; b < kMaxW; ++b) {
                 bar_init(&pub[s * kMaxW + b], 1);
@@ -239,8 +245,8 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
             ok = warp_wait(&pub[s * kMaxW + b], par, abort_flag, a.status);
             if (!ok) break;
             if (GP && b == 0) project(gs);
-            const int j1 = min(32 * b + 32, n);
-            for (int j = 32 * b; j < j1; ++j) {
+            const int j1 = bstart(b + 1);
+            for (int j = bstart(b); j < j1; ++j) {
                 const float* rv = rs + (size_t)j * kRS;
                 const float4* p4 = reinterpret_cast<const float4*>(rv);
                 float ga = 0.f, gb = 0.f, gc = 0.f, gd = 0.f;
@@ -297,7 +303,7 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
                 gd = fmaf(v.w, av[4 * l4 + 3], gd);
             }
             const float g = (ga + gb) + (gc + gd);
-            const float sig = __shfl_sync(FULL, g, j & 31);
+            const float sig = __shfl_sync(FULL, g, j - jb0);
             const int pr = pk(j, n);
             const float alpha = Rs[pr + j];
             __syncwarp();
@@ -352,7 +358,7 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
     __syncthreads();
     float* Rout = static_cast<float*>(a.R_out) + (size_t)cta * n * n;
     const int nn = n * n;
-    for (int e = c; e < nn; e += blockDim.x) {
+    for (int e = (int)threadIdx.x; e < nn; e += blockDim.x) {
         const int j = e / n, cc = e - j * n;
         Rout[e] = (cc >= j) ? Rs[pk(j, n) + cc] : 0.f;
     }
