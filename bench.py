@@ -482,6 +482,29 @@ def run_ours(args):
             pass
     K_spa = sorted(Ks["spa"][0].cpu().numpy().tolist())
 
+    # ---- the pass alone in each arithmetic form available for this n (the
+    # metric's "mixed vs FP32 at stated R error"), same resident X
+    forms = {}
+    for form in ("fp32", "tf32x3"):
+        if form == "tf32x3" and not (16 < n <= 64 and k <= 32):
+            continue
+        Rf = torch.empty((n, n), dtype=torch.float64, device=dev)
+        csf = torch.empty(n, dtype=torch.float64, device=dev)
+        GXf = torch.empty((k, n), dtype=torch.float64, device=dev)
+        h.tsqr_gp(Xd, k, w.seed, prec=form, out=(Rf, csf, GXf))
+        h.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            h.tsqr_gp(Xd, k, w.seed, prec=form, out=(Rf, csf, GXf))
+        e1.record(stream)
+        h.sync()
+        ms = e0.elapsed_time(e1) / reps
+        Rh = Rf.cpu().numpy()
+        forms[form] = {"pass_ms": ms, "GBps": bytes_step / ms / 1e6,
+                       "r_error_gram_identity": float(np.linalg.norm(Rh.T @ Rh - Gram) / np.linalg.norm(Gram))}
+
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
     if not args.no_e2e and not big:
@@ -515,7 +538,7 @@ def run_ours(args):
                            "l2": f"input ({bytes_step / 1e9:.2f} GB) larger than L2 (129 MB); no flush needed"},
                 "roofline": roofline, "roofline_other": roof_alu if roofline is roof_hbm else roof_hbm,
                 "leaf_ms": statistics.mean(leaf_ms), "r_error": r_err,
-                "K_spa": K_spa, "K_planted": P.K.tolist(),
+                "K_spa": K_spa, "K_planted": P.K.tolist(), "forms": forms,
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "cpu_baseline": cpu,
                 "wall_s_timed": t_wall}
         print(json.dumps(line), flush=True)
