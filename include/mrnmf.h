@@ -31,6 +31,7 @@
 #ifndef MRNMF_H
 #define MRNMF_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -219,6 +220,23 @@ mrnmf_status mrnmf_stream_push(mrnmf_handle* handle, const void* X_chunk, int64_
 mrnmf_status mrnmf_stream_end(mrnmf_handle* handle, double* R, double* colsum, double* GX, void* stream);
 
 /*
+ * Checkpoint of an open stream, between pushes (the analogue of re-running a
+ * failed map task, Sec. 3.5; the paper has no device counterpart).  The state
+ * is the running triangles, partial column sums and projections and the next
+ * global row index: O(P n^2) bytes, independent of the rows pushed.
+ *   state_size: bytes of the serialised state of the open stream.
+ *   state_save: copies it into `host` (>= state_size bytes, caller-owned) and
+ *               waits for `stream`.
+ *   state_load: restores it into an open stream begun with the same n, dtype,
+ *               prec, k and seed on the same device (else MRNMF_ERR_INVALID_ARG),
+ *               and waits for `stream`.  Pushing the remaining chunks then
+ *               gives bit for bit the result of the uninterrupted stream.
+ */
+mrnmf_status mrnmf_stream_state_size(mrnmf_handle* handle, size_t* bytes);
+mrnmf_status mrnmf_stream_state_save(mrnmf_handle* handle, void* host, size_t bytes, void* stream);
+mrnmf_status mrnmf_stream_state_load(mrnmf_handle* handle, const void* host, size_t bytes, void* stream);
+
+/*
  * Batched pass: R (and colsum) of many independent problems of uneven m and n
  * (Sec. 3.1's TSQR applied to each), FP32 form, enqueued on `stream` as a
  * handful of launches for the whole batch: the row streams of all problems
@@ -308,6 +326,17 @@ mrnmf_status mrnmf_profile_events(mrnmf_handle* handle, void* ev_start, void* ev
  */
 mrnmf_status mrnmf_tc_selftest(const float* A, const float* B, float* D, int32_t N, int32_t K, int32_t kind,
                                int32_t* status, void* stream);
+/*
+ * Failure injection (no counterpart in the paper): the bounded mbarrier wait
+ * of the warp-pipelined leaf, driven by a four-warp chain in one CTA in which
+ * warp v waits for warp v - 1, for at most v * limit_ns (limit_ns in
+ * [1e3, 1e9]).  The arrival on link `missing` (1..3; 0 = none) is left out,
+ * so that wait runs out and the waits after it are abandoned through the
+ * leaf's abort flag.  No fault, trap or hang is involved.
+ *   out    device int32[4] out: per warp 0 completed, 1 ran out, 2 abandoned.
+ *   status device int32 out: MRNMF_ERR_TIMEOUT when a wait ran out, else 0.
+ */
+mrnmf_status mrnmf_wait_selftest(int32_t missing, int64_t limit_ns, int32_t* out, int32_t* status, void* stream);
 uint64_t mrnmf_kernel_launches(void);
 
 #ifdef __cplusplus

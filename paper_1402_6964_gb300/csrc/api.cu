@@ -349,6 +349,100 @@ mrnmf_status mrnmf_stream_push(mrnmf_handle* h, const void* X_chunk, int64_t row
     return MRNMF_OK;
 }
 
+namespace {
+
+// Serialised streaming state: a header, then the running triangles, the
+// partial column sums and the partial projections, as they sit on the device.
+struct StreamStateHeader {
+    uint64_t magic;
+    int32_t n, k, P, fp64, tc, tri, xdtype, reserved;
+    uint64_t seed;
+    int64_t rows_seen;
+    uint64_t r_bytes, cs_bytes, gx_bytes;
+};
+constexpr uint64_t kStateMagic = 0x3154534D4E524D4Dull;  // "MMRNMST1"
+
+void state_parts(const mrnmf::PassState& st, uint64_t* rb, uint64_t* cb, uint64_t* gb)
+{
+    *rb = (uint64_t)(st.fp64 ? 8 : 4) * st.P * st.n * st.n;
+    *cb = 8ull * st.P * st.n;
+    *gb = st.k > 0 ? 8ull * st.P * st.k * st.n : 0;
+}
+
+}  // namespace
+
+mrnmf_status mrnmf_stream_state_size(mrnmf_handle* h, size_t* bytes)
+{
+    if (!h || !bytes) return MRNMF_ERR_INVALID_ARG;
+    if (!h->open) return fail(h, MRNMF_ERR_INVALID_ARG, "no open stream");
+    uint64_t rb, cb, gb;
+    state_parts(h->st, &rb, &cb, &gb);
+    *bytes = sizeof(StreamStateHeader) + rb + cb + gb;
+    return MRNMF_OK;
+}
+
+mrnmf_status mrnmf_stream_state_save(mrnmf_handle* h, void* host, size_t bytes, void* stream)
+{
+    if (!h || !host) return MRNMF_ERR_INVALID_ARG;
+    if (!h->open) return fail(h, MRNMF_ERR_INVALID_ARG, "no open stream");
+    size_t need = 0;
+    mrnmf_status s = mrnmf_stream_state_size(h, &need);
+    if (s != MRNMF_OK) return s;
+    if (bytes < need) return fail(h, MRNMF_ERR_INVALID_ARG, "state buffer too small");
+    if ((s = bind_device(h)) != MRNMF_OK) return s;
+    const mrnmf::PassState& st = h->st;
+    StreamStateHeader hd{};
+    hd.magic = kStateMagic;
+    hd.n = st.n;
+    hd.k = st.k;
+    hd.P = st.P;
+    hd.fp64 = st.fp64;
+    hd.tc = st.tc;
+    hd.tri = st.tri;
+    hd.xdtype = h->xdtype;
+    hd.seed = st.seed;
+    hd.rows_seen = st.rows_seen;
+    state_parts(st, &hd.r_bytes, &hd.cs_bytes, &hd.gx_bytes);
+    std::memcpy(host, &hd, sizeof(hd));
+    char* p = static_cast<char*>(host) + sizeof(hd);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(p, st.R, hd.r_bytes, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p + hd.r_bytes, st.cs, hd.cs_bytes, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess && hd.gx_bytes)
+        e = cudaMemcpyAsync(p + hd.r_bytes + hd.cs_bytes, st.gx, hd.gx_bytes, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    return e == cudaSuccess ? MRNMF_OK : cuda_fail(h, e, "state save");
+}
+
+mrnmf_status mrnmf_stream_state_load(mrnmf_handle* h, const void* host, size_t bytes, void* stream)
+{
+    if (!h || !host) return MRNMF_ERR_INVALID_ARG;
+    if (!h->open) return fail(h, MRNMF_ERR_INVALID_ARG, "no open stream (begin one with the saved parameters)");
+    if (bytes < sizeof(StreamStateHeader)) return fail(h, MRNMF_ERR_INVALID_ARG, "state buffer too small");
+    StreamStateHeader hd;
+    std::memcpy(&hd, host, sizeof(hd));
+    mrnmf::PassState& st = h->st;
+    uint64_t rb, cb, gb;
+    state_parts(st, &rb, &cb, &gb);
+    if (hd.magic != kStateMagic || hd.n != st.n || hd.k != st.k || hd.P != st.P || hd.fp64 != st.fp64 ||
+        hd.tc != st.tc || hd.xdtype != h->xdtype || hd.seed != st.seed || hd.r_bytes != rb || hd.cs_bytes != cb ||
+        hd.gx_bytes != gb)
+        return fail(h, MRNMF_ERR_INVALID_ARG, "saved state does not match the open stream's parameters");
+    if (bytes < sizeof(hd) + rb + cb + gb) return fail(h, MRNMF_ERR_INVALID_ARG, "state buffer too small");
+    mrnmf_status s = bind_device(h);
+    if (s != MRNMF_OK) return s;
+    const char* p = static_cast<const char*>(host) + sizeof(hd);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(st.R, p, rb, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st.cs, p + rb, cb, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && gb) e = cudaMemcpyAsync(st.gx, p + rb + cb, gb, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return cuda_fail(h, e, "state load");
+    st.tri = hd.tri;
+    st.rows_seen = hd.rows_seen;
+    return MRNMF_OK;
+}
+
 mrnmf_status mrnmf_stream_end(mrnmf_handle* h, double* R, double* colsum, double* GX, void* stream)
 {
     if (!h) return MRNMF_ERR_INVALID_ARG;

@@ -82,12 +82,15 @@ __device__ __forceinline__ void bar_arrive(uint64_t* b)
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
 }
 
-// Lane 0 waits for the phase of parity `par` to complete (bounded, and
-// abandoned at once when another warp has aborted); the outcome is
-// broadcast to the warp and ordered before the warp's later reads.
-__device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t par, volatile int* abort_flag, int* status)
+// Lane 0 waits for the phase of parity `par` to complete (bounded by
+// `limit_ns`, and abandoned at once when another warp has aborted); the
+// outcome is broadcast to the warp and ordered before the warp's later reads.
+// Returns 0 when the phase completed, 1 when this wait ran out (it then sets
+// the abort flag and MRNMF_ERR_TIMEOUT), 2 when it was abandoned.
+__device__ __forceinline__ int warp_wait_code(uint64_t* b, uint32_t par, volatile int* abort_flag, int* status,
+                                              uint64_t limit_ns)
 {
-    bool ok = true;
+    int code = 0;
     if ((threadIdx.x & 31) == 0) {
         const uint32_t a = saddr(b);
         const uint64_t t0 = gtime();
@@ -101,20 +104,54 @@ __device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t par, volatile in
                 : "memory");
             if (done) break;
             if (*abort_flag) {
-                ok = false;
+                code = 2;
                 break;
             }
-            if (gtime() - t0 > 1000000000ull) {
+            if (gtime() - t0 > limit_ns) {
                 *abort_flag = 1;
                 set_status(status, MRNMF_ERR_TIMEOUT);
-                ok = false;
+                code = 1;
                 break;
             }
         }
     }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
+    code = __shfl_sync(0xffffffffu, code, 0);
     __syncwarp();
-    return ok;
+    return code;
+}
+
+__device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t par, volatile int* abort_flag, int* status)
+{
+    return warp_wait_code(b, par, abort_flag, status, 1000000000ull) == 0;
+}
+
+// Failure injection for the hand-over above: four warps in a chain, warp v
+// (v >= 1) waiting on barrier v, which warp v - 1 arrives on once its own
+// wait has completed (warp 0 waits on nothing), with a limit of
+// v * limit_ns so that the order in which the waits give up is fixed.
+// Barrier `missing` (1..3; 0 = none) never gets its arrival: its wait runs
+// out, and the waits after it in the chain are abandoned through the abort
+// flag instead of running out in turn.  out[w]: 0 completed, 1 ran out,
+// 2 abandoned (warp 0 writes 0).
+__global__ void __launch_bounds__(128) wait_selftest_kernel(int missing, uint64_t limit_ns, int* out, int* status)
+{
+    __shared__ __align__(8) uint64_t bars[4];
+    __shared__ int abort_flag;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 4; ++i) bar_init(&bars[i], 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int code = 0;
+    if (w > 0) code = warp_wait_code(&bars[w], 0, &abort_flag, status, limit_ns * (uint64_t)w);
+    if (lane == 0) {
+        if (code == 0 && w + 1 < 4 && w + 1 != missing) bar_arrive(&bars[w + 1]);
+        out[w] = code;
+    }
+    // every barrier is either completed or abandoned before the CTA ends
+    __syncthreads();
 }
 
 // One stream (row range cta * rows_per_cta ..) of the problem in `a`; the
@@ -468,3 +505,16 @@ cudaError_t launch_pipe_leaf(const LeafArgs& a, int grid, cudaStream_t s)
 }
 
 }  // namespace mrnmf
+
+extern "C" mrnmf_status mrnmf_wait_selftest(int32_t missing, int64_t limit_ns, int32_t* out, int32_t* status,
+                                            void* stream)
+{
+    if (!out || !status || missing < 0 || missing > 3 || limit_ns < 1000 || limit_ns > 1000000000)
+        return MRNMF_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), s) != cudaSuccess) return MRNMF_ERR_CUDA;
+    mrnmf::wait_selftest_kernel<<<1, 128, 0, s>>>(missing, (uint64_t)limit_ns, reinterpret_cast<int*>(out),
+                                                  reinterpret_cast<int*>(status));
+    mrnmf::count_launch();
+    return cudaGetLastError() == cudaSuccess ? MRNMF_OK : MRNMF_ERR_CUDA;
+}

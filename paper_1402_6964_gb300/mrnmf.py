@@ -27,9 +27,9 @@ EXPORTS = [
     "mrnmf_create", "mrnmf_destroy", "mrnmf_last_error_string", "mrnmf_sync_status", "mrnmf_tsqr_r",
     "mrnmf_gauss_project", "mrnmf_tsqr_gp", "mrnmf_select_extreme", "mrnmf_nnls_h", "mrnmf_residual",
     "mrnmf_stream_begin", "mrnmf_stream_push", "mrnmf_stream_end", "mrnmf_factorize_host",
-    "mrnmf_profile_events", "mrnmf_kernel_launches", "mrnmf_tsqr_r_noalloc", "mrnmf_tc_selftest",
+    "mrnmf_profile_events", "mrnmf_kernel_launches", "mrnmf_tsqr_r_noalloc", "mrnmf_tc_selftest", "mrnmf_wait_selftest",
     "mrnmf_rank_sweep", "mrnmf_tsqr_r_batched", "mrnmf_gather_columns", "mrnmf_full_residual",
-    "mrnmf_r_svd",
+    "mrnmf_r_svd", "mrnmf_stream_state_size", "mrnmf_stream_state_save", "mrnmf_stream_state_load",
 ]
 
 
@@ -79,11 +79,15 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mrnmf_kernel_launches": ([], ctypes.c_uint64),
             "mrnmf_tsqr_r_noalloc": ([P, i64, i32, i64, P, P, P, P], st),
             "mrnmf_tc_selftest": ([P, P, P, i32, i32, i32, P, P], st),
+            "mrnmf_wait_selftest": ([i32, ctypes.c_int64, P, P, P], st),
             "mrnmf_rank_sweep": ([P, i32, P, i32, P, P, i32, i32, P, P, P], st),
             "mrnmf_tsqr_r_batched": ([P, P, i32, P], st),
             "mrnmf_gather_columns": ([P, P, i64, i32, i64, i32, P, i32, P, i64, P], st),
             "mrnmf_full_residual": ([P, P, i64, i32, i64, i32, P, i32, P, P, P], st),
             "mrnmf_r_svd": ([P, P, i32, P, P, P], st),
+            "mrnmf_stream_state_size": ([P, ctypes.POINTER(ctypes.c_size_t)], st),
+            "mrnmf_stream_state_save": ([P, P, ctypes.c_size_t, P], st),
+            "mrnmf_stream_state_load": ([P, P, ctypes.c_size_t, P], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -149,6 +153,19 @@ def tc_selftest(A, B, kind="tf32x3", status=None, stream=None):
     if st != OK:
         raise MrnmfError(st, "tc_selftest rejected its arguments")
     return D
+
+
+def wait_selftest(missing, limit_ns, device="cuda", stream=None):
+    """Failure injection on the leaf's bounded wait: returns the per-warp
+    outcome codes (0 completed, 1 ran out, 2 abandoned) and the status word,
+    both as device int32 tensors."""
+    import torch
+    out = torch.full((4,), -1, dtype=torch.int32, device=device)
+    status = torch.zeros(1, dtype=torch.int32, device=device)
+    st = int(load().mrnmf_wait_selftest(missing, limit_ns, _ptr(out), _ptr(status), _stream(stream)))
+    if st != OK:
+        raise MrnmfError(st, "wait_selftest rejected its arguments")
+    return out, status
 
 
 class Handle:
@@ -331,6 +348,19 @@ class Handle:
     def stream_push(self, X, stream=None):
         _check_X(X)
         self.check(self._lib.mrnmf_stream_push(self.h, _ptr(X), X.shape[0], X.stride(0), _stream(stream)))
+
+    def stream_state_save(self, stream=None) -> bytes:
+        """Checkpoint of the open stream (host bytes)."""
+        sz = ctypes.c_size_t(0)
+        self.check(self._lib.mrnmf_stream_state_size(self.h, ctypes.byref(sz)))
+        buf = ctypes.create_string_buffer(sz.value)
+        self.check(self._lib.mrnmf_stream_state_save(self.h, buf, sz.value, _stream(stream)))
+        return buf.raw
+
+    def stream_state_load(self, state: bytes, stream=None):
+        """Restore a checkpoint into a stream begun with the same parameters."""
+        buf = ctypes.create_string_buffer(state, len(state))
+        self.check(self._lib.mrnmf_stream_state_load(self.h, buf, len(state), _stream(stream)))
 
     def stream_end(self, n, k=0, device="cuda", stream=None):
         import torch

@@ -61,6 +61,14 @@ def test_argument_errors_need_no_device(lib):
     # streaming misuse
     assert lib.mrnmf_stream_push(h, dummy, 10, 8, None) == mrnmf.ERR_INVALID_ARG
     assert lib.mrnmf_stream_end(h, dummy, None, None, None) == mrnmf.ERR_INVALID_ARG
+    sz = ctypes.c_size_t(0)
+    assert lib.mrnmf_stream_state_size(h, ctypes.byref(sz)) == mrnmf.ERR_INVALID_ARG
+    assert lib.mrnmf_stream_state_save(h, dummy, 1 << 20, None) == mrnmf.ERR_INVALID_ARG
+    assert lib.mrnmf_stream_state_load(h, dummy, 1 << 20, None) == mrnmf.ERR_INVALID_ARG
+    # failure injection: a link outside 0..3, a limit outside [1e3, 1e9], NULL outputs
+    assert lib.mrnmf_wait_selftest(4, 5000000, dummy, dummy, None) == mrnmf.ERR_INVALID_ARG
+    assert lib.mrnmf_wait_selftest(1, 10, dummy, dummy, None) == mrnmf.ERR_INVALID_ARG
+    assert lib.mrnmf_wait_selftest(1, 5000000, None, dummy, None) == mrnmf.ERR_INVALID_ARG
     msg = lib.mrnmf_last_error_string(h)
     assert isinstance(msg, bytes) and len(msg) > 0
     lib.mrnmf_destroy(h)
