@@ -327,6 +327,18 @@ mrnmf_status mrnmf_profile_events(mrnmf_handle* handle, void* ev_start, void* ev
 mrnmf_status mrnmf_tc_selftest(const float* A, const float* B, float* D, int32_t N, int32_t K, int32_t kind,
                                int32_t* status, void* stream);
 /*
+ * Diagnostics (no counterpart in the paper): the scalars of one Householder
+ * step of the leaves, beta = -sign(alpha) sqrt(alpha^2 + sigma), d = alpha -
+ * beta, 1/beta, 1/d (Sec. 3.1), as the leaves compute them, next to the IEEE
+ * square root and reciprocals.
+ *   alpha, sigma device float[count] in (sigma > 0);
+ *   out device float[8 count] out: per argument pair the leaves' beta, d,
+ *   1/beta, 1/d, then the IEEE beta, d, 1/beta, 1/d.
+ */
+mrnmf_status mrnmf_hh_scalars_selftest(const float* alpha, const float* sigma, int64_t count, float* out,
+                                       void* stream);
+
+/*
  * Failure injection (no counterpart in the paper): the bounded mbarrier wait
  * of the warp-pipelined leaf, driven by a four-warp chain in one CTA in which
  * warp v waits for warp v - 1, for at most v * limit_ns (limit_ns in

@@ -346,13 +346,11 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
             __syncwarp();
             float beta = alpha, d = 0.f, rb = 0.f, rd = 0.f;
             if (sig > 0.f) {
-                // beta = -sign(alpha) sqrt(alpha^2 + sigma); reciprocals of beta
-                // and d = alpha - beta, never of their product
-                const float nrm = sqrtf(fmaf(alpha, alpha, sig));
-                beta = alpha >= 0.f ? -nrm : nrm;
-                d = alpha - beta;
-                rb = __frcp_rn(beta);
-                rd = __frcp_rn(d);
+                const HhScalars hs = hh_scalars(alpha, sig);
+                beta = hs.beta;
+                d = hs.d;
+                rb = hs.rb;
+                rd = hs.rd;
                 if (own && c > j) {
                     const float r = Rs[pr + c];
                     const float wp = fmaf(d, r, g);

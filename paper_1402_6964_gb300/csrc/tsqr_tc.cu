@@ -183,12 +183,8 @@ __device__ __forceinline__ void panel_steps(float* Pb, float* R, int j0, float* 
         const float gs = (rj[c] + rj[kNB + c]) + (rj[2 * kNB + c] + rj[3 * kNB + c]);
         const float sig = __shfl_sync(FULL, gs, j);
         if (sig > 0.f) {
-            const float nrm = sqrtf(fmaf(alpha, alpha, sig));
-            const float beta = alpha >= 0.f ? -nrm : nrm;
-            const float d = alpha - beta;
-            // reciprocals of beta and d, never of their product (which can
-            // underflow for a column already annihilated to rounding level)
-            const float rb = __frcp_rn(beta), rd = __frcp_rn(d);
+            const HhScalars hs = hh_scalars(alpha, sig);
+            const float beta = hs.beta, d = hs.d, rb = hs.rb, rd = hs.rd;
             if (c > j) {
                 const float wp = fmaf(d, rjc, gs);  // d (R_jc + g_c / d)
                 const float f = (wp * rd) * rb;

@@ -105,12 +105,9 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
     // w' = d R_jc + g_c (= d w), the reflector's action is
     // R_jc -= tau w  =  R_jc + w'/beta  and
     // A(:,c) -= tau s w A(:,j)  =  A(:,c) + (w'/d)(1/beta) A(:,j).
-    // Reciprocals of beta and d (never of their product, which can
-    // underflow for a column already annihilated to rounding level).  The
-    // square root and the reciprocals are correctly rounded: each stream's R
-    // takes tens of thousands of reflectors, and a beta a few ulp off makes
-    // each of them slightly non-orthogonal (measured: R error 13x larger with
-    // the SFU approximations at 1e7 x 50).
+    // beta, d and the reciprocals come from hh_scalars, accurate to the last
+    // bit (measured: R error 13x larger with the raw SFU approximations at
+    // 1e7 x 50).
     int j = 0;
     if (NC == 2) {
         // two live columns per lane while more than 32 columns remain (j < n - 32 <= 32)
@@ -137,10 +134,9 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
             __syncwarp();
             float beta = alpha;
             if (sig > 0.f) {
-                const float nrm = sqrtf(fmaf(alpha, alpha, sig));
-                beta = alpha >= 0.f ? -nrm : nrm;
-                const float d = alpha - beta;
-                const float rb = __frcp_rn(beta), rd = __frcp_rn(d);
+                const HhScalars hs = hh_scalars(alpha, sig);
+                beta = hs.beta;
+                const float d = hs.d, rb = hs.rb, rd = hs.rd;
                 float f0 = 0.f, f1 = 0.f;
                 if (own0 && c0 > j) {
                     const float r = Rw[pr + c0];
@@ -216,10 +212,9 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
         __syncwarp();
         float beta = alpha;
         if (sig > 0.f) {
-            const float nrm = sqrtf(fmaf(alpha, alpha, sig));
-            beta = alpha >= 0.f ? -nrm : nrm;
-            const float d = alpha - beta;
-            const float rb = __frcp_rn(beta), rd = __frcp_rn(d);
+            const HhScalars hs = hh_scalars(alpha, sig);
+            beta = hs.beta;
+            const float d = hs.d, rb = hs.rb, rd = hs.rd;
             float f0 = 0.f;
             if (om && cm > j) {
                 const float r = Rw[pr + cm];
@@ -787,11 +782,10 @@ __global__ void __launch_bounds__(256, KMAX <= 48 ? 2 : 1) tsqr_cta_kernel(const
             const int pr = pk_row(j, n);
             float beta = alpha;
             if (sig > 0.f) {
-                const float nrm = sqrtf(fmaf(alpha, alpha, sig));
-                beta = alpha >= 0.f ? -nrm : nrm;
+                const HhScalars hs = hh_scalars(alpha, sig);
+                beta = hs.beta;
                 if (own && c > j) {
-                    const float d = alpha - beta;
-                    const float rb = __frcp_rn(beta), rd = __frcp_rn(d);
+                    const float d = hs.d, rb = hs.rb, rd = hs.rd;
                     const float4* p4 = reinterpret_cast<const float4*>(pj);
                     float ga = 0.f, gb = 0.f, gc = 0.f, gd = 0.f;
 #pragma unroll

@@ -27,7 +27,7 @@ EXPORTS = [
     "mrnmf_create", "mrnmf_destroy", "mrnmf_last_error_string", "mrnmf_sync_status", "mrnmf_tsqr_r",
     "mrnmf_gauss_project", "mrnmf_tsqr_gp", "mrnmf_select_extreme", "mrnmf_nnls_h", "mrnmf_residual",
     "mrnmf_stream_begin", "mrnmf_stream_push", "mrnmf_stream_end", "mrnmf_factorize_host",
-    "mrnmf_profile_events", "mrnmf_kernel_launches", "mrnmf_tsqr_r_noalloc", "mrnmf_tc_selftest", "mrnmf_wait_selftest",
+    "mrnmf_profile_events", "mrnmf_kernel_launches", "mrnmf_tsqr_r_noalloc", "mrnmf_tc_selftest", "mrnmf_wait_selftest", "mrnmf_hh_scalars_selftest",
     "mrnmf_rank_sweep", "mrnmf_tsqr_r_batched", "mrnmf_gather_columns", "mrnmf_full_residual",
     "mrnmf_r_svd", "mrnmf_stream_state_size", "mrnmf_stream_state_save", "mrnmf_stream_state_load",
 ]
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mrnmf_tsqr_r_noalloc": ([P, i64, i32, i64, P, P, P, P], st),
             "mrnmf_tc_selftest": ([P, P, P, i32, i32, i32, P, P], st),
             "mrnmf_wait_selftest": ([i32, ctypes.c_int64, P, P, P], st),
+            "mrnmf_hh_scalars_selftest": ([P, P, i64, P, P], st),
             "mrnmf_rank_sweep": ([P, i32, P, i32, P, P, i32, i32, P, P, P], st),
             "mrnmf_tsqr_r_batched": ([P, P, i32, P], st),
             "mrnmf_gather_columns": ([P, P, i64, i32, i64, i32, P, i32, P, i64, P], st),
@@ -153,6 +154,18 @@ def tc_selftest(A, B, kind="tf32x3", status=None, stream=None):
     if st != OK:
         raise MrnmfError(st, "tc_selftest rejected its arguments")
     return D
+
+
+def hh_scalars_selftest(alpha, sigma, stream=None):
+    """The leaves' Householder scalars and the IEEE ones for float32 CUDA
+    `alpha`, `sigma`: a (count, 8) tensor, columns beta, d, 1/beta, 1/d of
+    the leaves, then of the IEEE operations."""
+    import torch
+    out = torch.empty((alpha.numel(), 8), dtype=torch.float32, device=alpha.device)
+    st = int(load().mrnmf_hh_scalars_selftest(_ptr(alpha), _ptr(sigma), alpha.numel(), _ptr(out), _stream(stream)))
+    if st != OK:
+        raise MrnmfError(st, "hh_scalars_selftest rejected its arguments")
+    return out
 
 
 def wait_selftest(missing, limit_ns, device="cuda", stream=None):

@@ -151,3 +151,24 @@ def test_missing_arrival_times_out(lib, oracle, missing, expect):
         R, cs = h.tsqr_r(dev(X))
         h.sync()
     assert rel_fro(host(R), oracle.qr_r(X.astype(np.float64))) <= 1e-5
+
+
+def test_householder_scalars_match_ieee(lib):
+    # the leaves' beta, d, 1/beta, 1/d (hardware approximations refined by one
+    # Newton step) against the IEEE square root and reciprocals: within one
+    # ulp everywhere, and equal for nearly all arguments
+    g = torch.Generator().manual_seed(5)
+    n = 1 << 20
+    alpha = (torch.rand(n, generator=g) * 2 - 1) * torch.pow(10.0, torch.rand(n, generator=g) * 24 - 12)
+    sigma = torch.pow(10.0, torch.rand(n, generator=g) * 30 - 15)
+    alpha[:1000] = 0.0                     # a column with a zero pivot
+    sigma[1000:2000] = alpha[1000:2000] ** 2 * 1e-12  # nearly annihilated columns
+    alpha, sigma = alpha.float().cuda(), sigma.float().cuda()
+    out = lib.hh_scalars_selftest(alpha, sigma)
+    torch.cuda.synchronize()
+    o = out.cpu()
+    ours, ieee = o[:, :4], o[:, 4:]
+    assert torch.isfinite(ours).all()
+    ulp = (ours.view(torch.int32).long() - ieee.view(torch.int32).long()).abs()
+    assert int(ulp.max()) <= 1
+    assert float((ulp == 0).double().mean()) >= 0.99
