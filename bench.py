@@ -382,16 +382,32 @@ def run_ours(args):
     Hs = {mth: torch.empty((r, n), dtype=torch.float64, device=dev) for mth in Ks}
     outs = {mth: torch.empty(2, dtype=torch.float64, device=dev) for mth in Ks}
 
+    # The three selections (and their NNLS and residual) depend only on R,
+    # the column sums and GX: each runs on its own CUDA stream with its own
+    # handle (a handle's small-step workspace serves one stream at a time),
+    # forked after the pass and joined before the step ends.
+    side = {mth: (torch.cuda.Stream(device=dev), mrnmf.Handle()) for mth in Ks}
+    ev_pass = torch.cuda.Event()
+    ev_side = {mth: torch.cuda.Event() for mth in Ks}
+
     def step():
         h.tsqr_gp(Xd, k, w.seed, prec=args.prec, out=(R, cs, GX))
-        for mth in ("spa", "xray", "gp"):
-            h.select_extreme(mth, R=R, colsum=cs, GX=GX if mth == "gp" else None, r=r, out=Ks[mth])
-            h.nnls_h(R, Ks[mth][0], out=Hs[mth])
-            h.residual(R, Ks[mth][0], Hs[mth], out=outs[mth])
+        ev_pass.record(stream)
+        for mth in ("xray", "spa", "gp"):
+            s, hm = side[mth]
+            s.wait_event(ev_pass)
+            hm.select_extreme(mth, R=R, colsum=cs, GX=GX if mth == "gp" else None, r=r, out=Ks[mth], stream=s)
+            hm.nnls_h(R, Ks[mth][0], out=Hs[mth], stream=s)
+            hm.residual(R, Ks[mth][0], Hs[mth], out=outs[mth], stream=s)
+            ev_side[mth].record(s)
+        for mth in ("xray", "spa", "gp"):
+            stream.wait_event(ev_side[mth])
 
     for _ in range(args.warmup):
         step()
     h.sync()
+    for _, hm in side.values():
+        hm.sync()
 
     leaf_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for a, b in leaf_ev:  # torch creates the CUDA event on first record; the library re-records it
@@ -419,6 +435,8 @@ def run_ours(args):
     launches = mrnmf.kernel_launches() - launches0
     h.profile_events(None, None)
     h.sync()
+    for _, hm in side.values():
+        hm.sync()
     t_dev = step_ev[0].elapsed_time(step_ev[-1]) / 1e3  # seconds
     leaf_ms = [a.elapsed_time(b) for a, b in leaf_ev]
     t_max = time_over_ranks(t_dev, world, dev)

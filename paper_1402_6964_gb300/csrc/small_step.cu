@@ -74,56 +74,71 @@ __device__ __forceinline__ double pick_gap(const Top2& t)
 }
 
 // ------------------------------------------------------------------------ SPA
-// One CTA; thread j owns column j of Y = R D^-1 (global scratch, row-major).
+// One CTA.  Column j of Y = R D^-1 is held by a group of G consecutive
+// threads (G divides 32), which split its rows: binary64 runs on few units
+// per SM on GB300, so the column work is spread over all four sub-partitions.
+// Y is kept column-major with an odd leading dimension, in shared memory when
+// it fits (else in the global scratch).
+template <int G>
 __global__ void __launch_bounds__(256) spa_kernel(const double* __restrict__ R, int n, const double* __restrict__ colsum,
                                                   int r, int32_t* __restrict__ K, double* __restrict__ gap,
-                                                  double* __restrict__ Y, int* status)
+                                                  double* __restrict__ Yg, int y_in_smem)
 {
+    extern __shared__ double ydyn[];
     __shared__ Top2 sh[8];
     __shared__ double u[MRNMF_NMAX];
     __shared__ int chosen[MRNMF_NMAX];
-    __shared__ double s_nrm, s_f0;
+    __shared__ double s_inv, s_f0;
     __shared__ int s_p;
-    const int j = threadIdx.x;
+    const unsigned FULL = 0xffffffffu;
+    const int ld = n | 1;
+    double* Y = y_in_smem ? ydyn : Yg;
+    const int t = threadIdx.x, j = t / G, part = t - j * G;
     const bool own = j < n;
-    if (own) {
-        chosen[j] = 0;
-        const double d = colsum[j];
-        for (int i = 0; i < n; ++i) Y[(size_t)i * n + j] = R[(size_t)i * n + j] / d;
+    for (int e = t; e < n * n; e += blockDim.x) {
+        const int i = e / n, c = e - i * n;
+        Y[(size_t)c * ld + i] = R[e] / colsum[c];
     }
+    for (int c = t; c < n; c += blockDim.x) chosen[c] = 0;
     __syncthreads();
-    for (int t = 0; t < r; ++t) {
-        double f = -INFINITY;
-        if (own && !chosen[j]) {
-            double s = 0.0;
-            for (int i = 0; i < n; ++i) {
-                const double y = Y[(size_t)i * n + j];
-                s += y * y;
-            }
-            f = s;
-        }
-        const Top2 b = block_top2(f, own && !chosen[j] ? j : INT_MAX, sh);
-        if (j == 0) {
+    for (int step = 0; step < r; ++step) {
+        const bool cand = own && !chosen[j];
+        const double* yj = Y + (size_t)(own ? j : 0) * ld;
+        double f = 0.0;
+        if (cand)
+            for (int i = part; i < n; i += G) f = fma(yj[i], yj[i], f);
+#pragma unroll
+        for (int o = G / 2; o; o >>= 1) f += __shfl_xor_sync(FULL, f, o);
+        const bool lead = cand && part == 0;
+        const Top2 b = block_top2(lead ? f : -INFINITY, lead ? j : INT_MAX, sh);
+        if (t == 0) {
             const int p = b.i1;
-            if (t == 0) s_f0 = b.b1;
+            if (step == 0) s_f0 = b.b1;
             double g = pick_gap(b);
             if (!(b.b1 > 1e-24 * s_f0)) g = -1.0;
-            K[t] = p;
-            if (gap) gap[t] = g;
+            K[step] = p;
+            if (gap) gap[step] = g;
             chosen[p] = 1;
             s_p = p;
-            s_nrm = sqrt(b.b1);
+            const double nrm = sqrt(b.b1);
+            s_inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
         }
         __syncthreads();
         const int p = s_p;
-        const double nrm = s_nrm;
-        if (!(nrm > 0.0)) continue;
-        if (own) u[j] = Y[(size_t)j * n + p] / nrm;
+        const double inv = s_inv;
+        if (!(inv > 0.0)) continue;
+        for (int i = t; i < n; i += blockDim.x) u[i] = Y[(size_t)p * ld + i] * inv;
         __syncthreads();
-        if (own) {
-            double cj = 0.0;
-            for (int i = 0; i < n; ++i) cj += u[i] * Y[(size_t)i * n + j];
-            for (int i = 0; i < n; ++i) Y[(size_t)i * n + j] -= cj * u[i];
+        // project the chosen direction out of the remaining candidates
+        const bool upd = own && !chosen[j];
+        double c = 0.0;
+        if (upd)
+            for (int i = part; i < n; i += G) c = fma(u[i], yj[i], c);
+#pragma unroll
+        for (int o = G / 2; o; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+        if (upd) {
+            double* yw = Y + (size_t)j * ld;
+            for (int i = part; i < n; i += G) yw[i] = fma(-c, u[i], yw[i]);
         }
         __syncthreads();
     }
@@ -362,9 +377,10 @@ __device__ __forceinline__ double rsqrt_d(double d)
 // Lawson-Hanson inner loop before the usual outer iterations, so the result
 // is the same minimiser (unique when R(:,K) has full column rank).  H is read
 // and then overwritten, column by column (one warp per column).
-// The normal equations are formed here (the same sums, in the same order, as
-// nnls_gram_kernel): A'A = R(:,K)'R(:,K) in shared memory per block, and per
-// column A'b = R(:,K)'R(:,c) and b'b = |R(:,c)|^2.
+// The normal equations are formed here: A'A = R(:,K)'R(:,K) in shared
+// memory per block (the same sums, in the same order, as nnls_gram_kernel),
+// and per column A'b = R(:,K)'R(:,c) and b'b = |R(:,c)|^2 (b'b only sets
+// the dual tolerance).
 __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restrict__ R,
                                                            const int32_t* __restrict__ K, int r, int n,
                                                            double* __restrict__ H, int r0, int* status)
@@ -392,8 +408,11 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
     }
     double maxdiag = act ? AtA[lane * r + lane] : 0.0;
     for (int o = 16; o; o >>= 1) maxdiag = fmax(maxdiag, __shfl_xor_sync(FULL, maxdiag, o));
+    // b'b = |R(:,c)|^2, the rows split over the lanes (binary64 issues
+    // slowly on GB300: seven instructions instead of n)
     double bb = 0.0;
-    for (int i = 0; i < n; ++i) bb += R[(size_t)i * n + c] * R[(size_t)i * n + c];
+    for (int i = lane; i < n; i += 32) bb = fma(R[(size_t)i * n + c], R[(size_t)i * n + c], bb);
+    for (int o = 16; o; o >>= 1) bb += __shfl_xor_sync(FULL, bb, o);
     const double tol = 1e-12 * sqrt(maxdiag * (bb > 0.0 ? bb : 0.0));
     double x = 0.0;
     bool passive = false;
@@ -759,12 +778,14 @@ __global__ void __launch_bounds__(256) xray_pick_kernel(const double* __restrict
     // second-best within the thread's own strided set is folded by the block merge
     Top2 b = block_top2(v, idx, sh);
     if (threadIdx.x == 0) {
-        // the strided pre-pass may hide a per-thread runner-up; recompute the
-        // runner-up exactly
-        double second = -INFINITY;
-        for (int j = 0; j < n; ++j)
-            if (!chosen[j] && j != b.i1) second = fmax(second, score[j]);
-        b.b2 = second;
+        // with more candidates than threads the strided pre-pass may hide a
+        // per-thread runner-up: recompute it (n <= blockDim: the merge is exact)
+        if (n > (int)blockDim.x) {
+            double second = -INFINITY;
+            for (int j = 0; j < n; ++j)
+                if (!chosen[j] && j != b.i1) second = fmax(second, score[j]);
+            b.b2 = second;
+        }
         if (t == 0) *s0 = b.b1;
         double g = pick_gap(b);
         if (!(b.b1 > 1e-12 * (*s0))) g = -1.0;
@@ -964,10 +985,26 @@ size_t small_ws_bytes(int n, int k, int r)
 cudaError_t select_spa(const double* R, int n, const double* colsum, int r, int32_t* K, double* gap, void* ws,
                        int* status, cudaStream_t s)
 {
+    (void)status;
     SmallWs w = carve(ws, n, r);
-    spa_kernel<<<1, ((n + 31) / 32) * 32, 0, s>>>(R, n, colsum, r, K, gap, w.Y, status);
-    count_launch();
-    return cudaGetLastError();
+    const int G = n <= 32 ? 8 : n <= 64 ? 4 : n <= 128 ? 2 : 1;
+    const int threads = ((G * n + 31) / 32) * 32;
+    const size_t ybytes = sizeof(double) * (size_t)n * (n | 1);
+    const int in_smem = ybytes <= 160 * 1024;
+    const size_t smem = in_smem ? ybytes : 0;
+    auto launch = [&](auto kern) -> cudaError_t {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        kern<<<1, threads, smem, s>>>(R, n, colsum, r, K, gap, w.Y, in_smem);
+        count_launch();
+        return cudaGetLastError();
+    };
+    if (G == 8) return launch(spa_kernel<8>);
+    if (G == 4) return launch(spa_kernel<4>);
+    if (G == 2) return launch(spa_kernel<2>);
+    return launch(spa_kernel<1>);
 }
 
 cudaError_t select_xray(const double* R, int n, int r, int32_t* K, double* gap, void* ws, int* status,

@@ -450,7 +450,7 @@ __device__ __forceinline__ void warp_stream_body(const LeafArgs& a, const int ct
 
 
 template <int NC, int L, bool GP>
-__global__ void __launch_bounds__(kWarps * 32) tsqr_warp_kernel(const LeafArgs a)
+__global__ void __launch_bounds__(kWarps * 32, (L == 32 || (NC == 1 && L == 64)) ? 3 : 1) tsqr_warp_kernel(const LeafArgs a)
 {
     warp_stream_body<NC, L, GP>(a, blockIdx.x);
 }
