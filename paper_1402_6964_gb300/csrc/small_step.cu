@@ -167,6 +167,7 @@ __global__ void nnls_gram_kernel(const double* __restrict__ R, int n, const int3
             dst = btb + ca;
         }
         double s = 0.0;
+        #pragma unroll 8  // keep eight loads in flight: each is an L2 round trip
         for (int i = 0; i < n; ++i) s += R[(size_t)i * n + ca] * R[(size_t)i * n + cb];
         *dst = s;
     }
@@ -392,6 +393,7 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
     for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
         const int ca = Ks[e / r], cb = Ks[e % r];
         double sum = 0.0;
+        #pragma unroll 8  // keep eight loads in flight: each is an L2 round trip
         for (int i = 0; i < n; ++i) sum += R[(size_t)i * n + ca] * R[(size_t)i * n + cb];
         AtA[e] = sum;
     }
@@ -404,6 +406,7 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
     double rhs = 0.0;
     if (act) {
         const int ca = Ks[lane];
+        #pragma unroll 8  // keep eight loads in flight: each is an L2 round trip
         for (int i = 0; i < n; ++i) rhs += R[(size_t)i * n + ca] * R[(size_t)i * n + c];
     }
     double maxdiag = act ? AtA[lane * r + lane] : 0.0;
@@ -684,6 +687,7 @@ __global__ void residual_partial_kernel(const double* __restrict__ R, int n, con
         const int i = o / n, c = o - i * n;
         const double v = R[o];
         double s = v;
+        #pragma unroll 8  // keep eight loads in flight: each is an L2 round trip
         for (int a = 0; a < r; ++a) s -= R[(size_t)i * n + K[a]] * H[(size_t)a * n + c];
         e2 = s * s;
         r2 = v * v;
@@ -737,6 +741,7 @@ __global__ void __launch_bounds__(256) xray_score_kernel(const double* __restric
     double acc = 0.0, cn = 0.0;
     for (int q = threadIdx.x; q < n; q += blockDim.x) {
         double v = 0.0;
+        #pragma unroll 8  // keep eight loads in flight: each is an L2 round trip
         for (int i = 0; i < n; ++i) v += Res[(size_t)i * n + q] * R[(size_t)i * n + j];
         acc += v * v;
     }
@@ -803,6 +808,7 @@ __global__ void xray_res_kernel(const double* __restrict__ R, int n, const int32
     if (o >= n * n) return;
     const int i = o / n, c = o - i * n;
     double s = R[o];
+    #pragma unroll 8  // keep eight loads in flight: each is an L2 round trip
     for (int a = 0; a < t; ++a) s -= R[(size_t)i * n + K[a]] * H[(size_t)a * n + c];
     Res[o] = s;
 }
@@ -824,12 +830,23 @@ __global__ void __launch_bounds__(256) gp_select_kernel(const double* __restrict
 {
     __shared__ int jmax_s[MRNMF_KMAX], jmin_s[MRNMF_KMAX];
     __shared__ double gmax_s[MRNMF_KMAX], gmin_s[MRNMF_KMAX];
+    __shared__ int Ks[MRNMF_NMAX];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kPer = MRNMF_NMAX / 32;  // row entries per lane
     for (int l = warp; l < k; l += blockDim.x >> 5) {
         double zmax = -INFINITY, zmin = INFINITY, scale = 0.0;
         int imax = INT_MAX, imin = INT_MAX;
-        for (int j = lane; j < n; j += 32) {
-            const double z = GX[(size_t)l * n + j] / colsum[j];
+        double zl[kPer];  // the lane's entries of row l of GX D^-1, formed once
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int j = lane + 32 * q;
+            zl[q] = j < n ? GX[(size_t)l * n + j] / colsum[j] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int j = lane + 32 * q;
+            if (j >= n) break;
+            const double z = zl[q];
             if (z > zmax) {
                 zmax = z;
                 imax = j;
@@ -856,8 +873,11 @@ __global__ void __launch_bounds__(256) gp_select_kernel(const double* __restrict
             scale = fmax(scale, __shfl_xor_sync(0xffffffffu, scale, o));
         }
         double s2max = -INFINITY, s2min = INFINITY;
-        for (int j = lane; j < n; j += 32) {
-            const double z = GX[(size_t)l * n + j] / colsum[j];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int j = lane + 32 * q;
+            if (j >= n) break;
+            const double z = zl[q];
             if (j != imax) s2max = fmax(s2max, z);
             if (j != imin) s2min = fmin(s2min, z);
         }
@@ -874,6 +894,7 @@ __global__ void __launch_bounds__(256) gp_select_kernel(const double* __restrict
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        // the list is built in shared memory (every duplicate check reads it)
         int cnt = 0;
         for (int l = 0; l < k && cnt < r; ++l) {
             const int picks[2] = {jmax_s[l], jmin_s[l]};
@@ -881,19 +902,21 @@ __global__ void __launch_bounds__(256) gp_select_kernel(const double* __restrict
             for (int q = 0; q < 2 && cnt < r; ++q) {
                 bool dup = false;
                 for (int c = 0; c < cnt; ++c)
-                    if (K[c] == picks[q]) dup = true;
+                    if (Ks[c] == picks[q]) dup = true;
                 if (!dup) {
                     if (gap) gap[cnt] = pg[q];
-                    K[cnt++] = picks[q];
+                    Ks[cnt++] = picks[q];
                 }
             }
         }
         for (int t = cnt; t < r; ++t) {
-            K[t] = -1;
+            Ks[t] = -1;
             if (gap) gap[t] = -1.0;
         }
         if (cnt < r) set_status(status, MRNMF_ERR_RANK_DEFICIENT);
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < r; t += blockDim.x) K[t] = Ks[t];
 }
 
 // Workspace layout of the small step.

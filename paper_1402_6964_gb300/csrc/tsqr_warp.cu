@@ -513,18 +513,19 @@ __device__ __forceinline__ void tree_wide_body(const float* __restrict__ Rin, in
         const int b = j & 1;
         float4* pv = reinterpret_cast<float4*>(&piv[b][sgm][0]);
         if (c == j) {
-            float sg = 0.f;
+            // four partial sums: the pivot's squared norm is on the step's critical path
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
             for (int q = 0; q < NP / 4; ++q) {
                 if (4 * q > j) break;
                 const float4 v = make_float4(col[4 * q], col[4 * q + 1], col[4 * q + 2], col[4 * q + 3]);
-                sg = fmaf(v.x, v.x, sg);
-                sg = fmaf(v.y, v.y, sg);
-                sg = fmaf(v.z, v.z, sg);
-                sg = fmaf(v.w, v.w, sg);
+                s0 = fmaf(v.x, v.x, s0);
+                s1 = fmaf(v.y, v.y, s1);
+                s2 = fmaf(v.z, v.z, s2);
+                s3 = fmaf(v.w, v.w, s3);
                 pv[q] = v;
             }
-            sig[b][sgm] = sg;
+            sig[b][sgm] = (s0 + s1) + (s2 + s3);
         }
         __syncthreads();
         float sigma = 0.f;
@@ -532,14 +533,17 @@ __device__ __forceinline__ void tree_wide_body(const float* __restrict__ Rin, in
         for (int q = 0; q < S; ++q) sigma += sig[b][q];
         const int pr = pk_row(j, n);
         const float alpha = Rs[pr + j];
-        float beta = alpha, tau = 0.f, scale = 0.f;
+        // the leaves' column step: with w' = d R_jc + g_c, R_jc += w'/beta and
+        // column c += (w'/d)(1/beta) times the raw pivot column
+        float beta = alpha, d = 0.f, rb = 0.f, rd = 0.f;
         if (sigma > 0.f) {
-            const float nrm = sqrtf(alpha * alpha + sigma);
-            beta = alpha >= 0.f ? -nrm : nrm;
-            scale = 1.f / (alpha - beta);
-            tau = (beta - alpha) / beta;
+            const HhScalars hs = hh_scalars(alpha, sigma);
+            beta = hs.beta;
+            d = hs.d;
+            rb = hs.rb;
+            rd = hs.rd;
         }
-        const bool upd = tau != 0.f && c > j && c < n;
+        const bool upd = sigma > 0.f && c > j && c < n;
         const float r = upd ? Rs[pr + c] : 0.f;  // read before the barrier: segment 0 rewrites it after
         if (upd) {
             float d0 = 0.f, d1 = 0.f;
@@ -559,18 +563,18 @@ __device__ __forceinline__ void tree_wide_body(const float* __restrict__ Rin, in
             float dsum = 0.f;
 #pragma unroll
             for (int q = 0; q < S; ++q) dsum += dpart[b][q][c];
-            const float w = fmaf(scale, dsum, r);
-            const float f = tau * w * scale;
+            const float wp = fmaf(d, r, dsum);
+            const float f = (wp * rd) * rb;
 #pragma unroll
             for (int q = 0; q < NP / 4; ++q) {
                 if (4 * q > j) break;
                 const float4 v = pv[q];
-                col[4 * q] = fmaf(-f, v.x, col[4 * q]);
-                col[4 * q + 1] = fmaf(-f, v.y, col[4 * q + 1]);
-                col[4 * q + 2] = fmaf(-f, v.z, col[4 * q + 2]);
-                col[4 * q + 3] = fmaf(-f, v.w, col[4 * q + 3]);
+                col[4 * q] = fmaf(f, v.x, col[4 * q]);
+                col[4 * q + 1] = fmaf(f, v.y, col[4 * q + 1]);
+                col[4 * q + 2] = fmaf(f, v.z, col[4 * q + 2]);
+                col[4 * q + 3] = fmaf(f, v.w, col[4 * q + 3]);
             }
-            if (sgm == 0) Rs[pr + c] = fmaf(-tau, w, r);
+            if (sgm == 0) Rs[pr + c] = fmaf(wp, rb, r);
         }
         if (c == j && sgm == 0) Rs[pr + j] = beta;
         // the next step writes the other buffers; this step's readers are past the barrier above
