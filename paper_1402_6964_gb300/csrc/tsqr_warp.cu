@@ -114,6 +114,11 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
         const int jm = n - 32;
         for (; j < jm; ++j) {
             const float4* pj = reinterpret_cast<const float4*>(pub + (j & 1) * L);
+            // row j of R: only this step writes it, so it is read before the dot
+            // (off the step's critical path)
+            const int pr = pk_row(j, n);
+            const float alpha = Rw[pr + j];
+            const float r0v = own0 ? Rw[pr + c0] : 0.f, r1v = own1 ? Rw[pr + c1] : 0.f;
             float g0a = 0.f, g0b = 0.f, g0c = 0.f, g0d = 0.f, g1a = 0.f, g1b = 0.f, g1c = 0.f, g1d = 0.f;
 #pragma unroll
             for (int l4 = 0; l4 < L / 4; ++l4) {
@@ -129,8 +134,6 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
             }
             const float g0 = (g0a + g0b) + (g0c + g0d), g1 = (g1a + g1b) + (g1c + g1d);
             const float sig = __shfl_sync(FULL, g0, j);
-            const int pr = pk_row(j, n);
-            const float alpha = Rw[pr + j];
             __syncwarp();
             float beta = alpha;
             if (sig > 0.f) {
@@ -139,16 +142,14 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
                 const float d = hs.d, rb = hs.rb, rd = hs.rd;
                 float f0 = 0.f, f1 = 0.f;
                 if (own0 && c0 > j) {
-                    const float r = Rw[pr + c0];
-                    const float wp = fmaf(d, r, g0);
+                    const float wp = fmaf(d, r0v, g0);
                     f0 = (wp * rd) * rb;
-                    Rw[pr + c0] = fmaf(wp, rb, r);
+                    Rw[pr + c0] = fmaf(wp, rb, r0v);
                 }
                 if (own1) {
-                    const float r = Rw[pr + c1];
-                    const float wp = fmaf(d, r, g1);
+                    const float wp = fmaf(d, r1v, g1);
                     f1 = (wp * rd) * rb;
-                    Rw[pr + c1] = fmaf(wp, rb, r);
+                    Rw[pr + c1] = fmaf(wp, rb, r1v);
                 }
 #pragma unroll
                 for (int l4 = 0; l4 < L / 4; ++l4) {
@@ -191,6 +192,9 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
     const bool om = NC == 2 ? true : own0;
     for (; j < n; ++j) {
         const float4* pj = reinterpret_cast<const float4*>(pub + (j & 1) * L);
+        const int pr = pk_row(j, n);
+        const float alpha = Rw[pr + j];
+        const float rmv = om ? Rw[pr + cm] : 0.f;
         // short tiles keep the pivot in registers for the update (one read of
         // the publication buffer per step instead of two)
         constexpr bool kPivReg = L <= 64;
@@ -207,8 +211,6 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
         }
         const float g0 = (g0a + g0b) + (g0c + g0d);
         const float sig = __shfl_sync(FULL, g0, j & 31);
-        const int pr = pk_row(j, n);
-        const float alpha = Rw[pr + j];
         __syncwarp();
         float beta = alpha;
         if (sig > 0.f) {
@@ -217,10 +219,9 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
             const float d = hs.d, rb = hs.rb, rd = hs.rd;
             float f0 = 0.f;
             if (om && cm > j) {
-                const float r = Rw[pr + cm];
-                const float wp = fmaf(d, r, g0);
+                const float wp = fmaf(d, rmv, g0);
                 f0 = (wp * rd) * rb;
-                Rw[pr + cm] = fmaf(wp, rb, r);
+                Rw[pr + cm] = fmaf(wp, rb, rmv);
             }
 #pragma unroll
             for (int l4 = 0; l4 < L / 4; ++l4) {
@@ -449,8 +450,12 @@ __device__ __forceinline__ void warp_stream_body(const LeafArgs& a, const int ct
 }
 
 
+// Residency targets (measured): the 32-row forms run three CTAs per SM with
+// the projection (shared memory allows no more) and four without it (n up to
+// about 56 fits four in shared memory); the one-column 64-row form three.
 template <int NC, int L, bool GP>
-__global__ void __launch_bounds__(kWarps * 32, (L == 32 || (NC == 1 && L == 64)) ? 3 : 1) tsqr_warp_kernel(const LeafArgs a)
+__global__ void __launch_bounds__(kWarps * 32, (L == 32 && !GP) ? 4 : (L == 32 || (NC == 1 && L == 64)) ? 3 : 1)
+    tsqr_warp_kernel(const LeafArgs a)
 {
     warp_stream_body<NC, L, GP>(a, blockIdx.x);
 }
