@@ -190,7 +190,9 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
     }
     const int cm = (NC == 2 && lane < n - 32) ? lane + 32 : lane;  // the lane's live column
     const bool om = NC == 2 ? true : own0;
-    for (; j < n; ++j) {
+    // one column per lane until at most 16 columns remain (the split form below)
+    const int jsplit = n - 16 > j ? n - 16 : j;
+    for (; j < jsplit; ++j) {
         const float4* pj = reinterpret_cast<const float4*>(pub + (j & 1) * L);
         const int pr = pk_row(j, n);
         const float alpha = Rw[pr + j];
@@ -238,6 +240,75 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
             float4* dst = reinterpret_cast<float4*>(pub + (jn & 1) * L);
 #pragma unroll
             for (int l4 = 0; l4 < L / 4; ++l4)
+                dst[l4] = make_float4(a0[4 * l4], a0[4 * l4 + 1], a0[4 * l4 + 2], a0[4 * l4 + 3]);
+        }
+        __syncwarp();
+    }
+    if (j >= n) return;
+    // Split form for the last (at most 16) columns: column jsplit + q is held
+    // by lanes q and q + 16, which own rows [0, L/2) and [L/2, L) of it, so a
+    // step costs half the FMAs; the two halves of each dot product are summed
+    // with one shuffle.  The columns move here from lane (c & 31).
+    constexpr int LH = L / 2;
+    const int hf = lane >> 4, q = lane & 15;
+    const int cq = jsplit + q;
+    const bool oq = cq < n;
+    {
+        const int src = cq & 31;
+#pragma unroll
+        for (int i = 0; i < LH; ++i) {
+            const float lo = __shfl_sync(FULL, a0[i], src);
+            const float hi = __shfl_sync(FULL, a0[LH + i], src);
+            a0[i] = hf ? hi : lo;
+        }
+    }
+    for (; j < n; ++j) {
+        const float4* pj = reinterpret_cast<const float4*>(pub + (j & 1) * L + hf * LH);
+        const int pr = pk_row(j, n);
+        const float alpha = Rw[pr + j];
+        const float rq = oq ? Rw[pr + cq] : 0.f;
+        constexpr bool kPivReg = LH <= 32;
+        float4 pv[kPivReg ? LH / 4 : 1];
+        float g0a = 0.f, g0b = 0.f, g0c = 0.f, g0d = 0.f;
+#pragma unroll
+        for (int l4 = 0; l4 < LH / 4; ++l4) {
+            const float4 v = pj[l4];
+            if (kPivReg) pv[kPivReg ? l4 : 0] = v;
+            g0a = fmaf(v.x, a0[4 * l4], g0a);
+            g0b = fmaf(v.y, a0[4 * l4 + 1], g0b);
+            g0c = fmaf(v.z, a0[4 * l4 + 2], g0c);
+            g0d = fmaf(v.w, a0[4 * l4 + 3], g0d);
+        }
+        float g0 = (g0a + g0b) + (g0c + g0d);
+        g0 += __shfl_xor_sync(FULL, g0, 16);
+        const float sig = __shfl_sync(FULL, g0, j - jsplit);
+        __syncwarp();
+        float beta = alpha;
+        if (sig > 0.f) {
+            const HhScalars hs = hh_scalars(alpha, sig);
+            beta = hs.beta;
+            const float d = hs.d, rb = hs.rb, rd = hs.rd;
+            float f0 = 0.f;
+            if (oq && cq > j) {
+                const float wp = fmaf(d, rq, g0);
+                f0 = (wp * rd) * rb;
+                if (hf == 0) Rw[pr + cq] = fmaf(wp, rb, rq);
+            }
+#pragma unroll
+            for (int l4 = 0; l4 < LH / 4; ++l4) {
+                const float4 v = kPivReg ? pv[kPivReg ? l4 : 0] : pj[l4];
+                a0[4 * l4] = fmaf(f0, v.x, a0[4 * l4]);
+                a0[4 * l4 + 1] = fmaf(f0, v.y, a0[4 * l4 + 1]);
+                a0[4 * l4 + 2] = fmaf(f0, v.z, a0[4 * l4 + 2]);
+                a0[4 * l4 + 3] = fmaf(f0, v.w, a0[4 * l4 + 3]);
+            }
+        }
+        if (lane == j - jsplit) Rw[pr + j] = beta;
+        const int jn = j + 1;
+        if (jn < n && q == jn - jsplit) {  // both halves of the next pivot publish
+            float4* dst = reinterpret_cast<float4*>(pub + (jn & 1) * L + hf * LH);
+#pragma unroll
+            for (int l4 = 0; l4 < LH / 4; ++l4)
                 dst[l4] = make_float4(a0[4 * l4], a0[4 * l4 + 1], a0[4 * l4 + 2], a0[4 * l4 + 3]);
         }
         __syncwarp();
