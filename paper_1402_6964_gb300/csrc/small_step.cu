@@ -727,68 +727,76 @@ __global__ void residual_final_kernel(const double* __restrict__ part, int nb, d
 }
 
 // ----------------------------------------------------------------------- XRAY
-// score_j = ||Res^T R(:,j)|| / ||R(:,j)|| for unchosen j (one block per j).
-__global__ void __launch_bounds__(256) xray_score_kernel(const double* __restrict__ R, const double* __restrict__ Res,
-                                                         int n, const int* __restrict__ chosen,
-                                                         double* __restrict__ score)
+// One launch per pick: block j scores candidate j,
+//   score_j = ||Res^T R(:,j)|| / ||R(:,j)||  (unchosen j; -inf otherwise),
+// and the last block to finish (a ticket counter) picks the argmax, so the
+// pick needs no launch of its own.  The counter is zero on entry and left at
+// zero.
+__global__ void __launch_bounds__(128) xray_score_pick_kernel(const double* __restrict__ R,
+                                                              const double* __restrict__ Res, int n,
+                                                              int* __restrict__ chosen, double* __restrict__ score,
+                                                              int t, int32_t* __restrict__ K,
+                                                              double* __restrict__ gap, double* __restrict__ s0,
+                                                              int* __restrict__ ticket)
 {
     __shared__ double sh[8];
+    __shared__ Top2 sht[8];
+    __shared__ int last;
     const int j = blockIdx.x;
-    if (chosen[j]) {
-        if (threadIdx.x == 0) score[j] = -INFINITY;
-        return;
-    }
-    double acc = 0.0, cn = 0.0;
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
-        double v = 0.0;
-        #pragma unroll 8  // keep eight loads in flight: each is an L2 round trip
-        for (int i = 0; i < n; ++i) v += Res[(size_t)i * n + q] * R[(size_t)i * n + j];
-        acc += v * v;
-    }
-    if (threadIdx.x < 32) {
-        for (int i = threadIdx.x; i < n; i += 32) {
-            const double x = R[(size_t)i * n + j];
-            cn += x * x;
+    if (!chosen[j]) {
+        double acc = 0.0, cn = 0.0;
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+            double v = 0.0;
+#pragma unroll 8  // keep eight loads in flight: each is an L2 round trip
+            for (int i = 0; i < n; ++i) v += Res[(size_t)i * n + q] * R[(size_t)i * n + j];
+            acc += v * v;
         }
-        cn = warp_sum(cn);
+        if (threadIdx.x < 32) {
+            for (int i = threadIdx.x; i < n; i += 32) {
+                const double x = R[(size_t)i * n + j];
+                cn += x * x;
+            }
+            cn = warp_sum(cn);
+        }
+        acc = warp_sum(acc);
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 0) sh[w] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) sum += sh[q];
+            const double nrm = sqrt(cn);
+            score[j] = nrm > 0.0 ? sqrt(sum) / nrm : 0.0;
+        }
+    } else if (threadIdx.x == 0) {
+        score[j] = -INFINITY;
     }
-    acc = warp_sum(acc);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) sh[w] = acc;
+    // the last block to finish picks
+    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += sh[q];
-        const double nrm = sqrt(cn);
-        score[j] = nrm > 0.0 ? sqrt(s) / nrm : 0.0;
-    }
-}
-
-__global__ void __launch_bounds__(256) xray_pick_kernel(const double* __restrict__ score, int n, int t,
-                                                        int* __restrict__ chosen, int32_t* __restrict__ K,
-                                                        double* __restrict__ gap, double* __restrict__ s0)
-{
-    __shared__ Top2 sh[8];
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1) == n - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
     double v = -INFINITY;
     int idx = INT_MAX;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        if (!chosen[j]) {
-            const double s = score[j];
-            if (idx == INT_MAX || s > v) {
-                v = s;
-                idx = j;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        if (!chosen[c]) {
+            const double sc = __ldcg(score + c);
+            if (idx == INT_MAX || sc > v) {
+                v = sc;
+                idx = c;
             }
         }
     }
-    // second-best within the thread's own strided set is folded by the block merge
-    Top2 b = block_top2(v, idx, sh);
+    Top2 b = block_top2(v, idx, sht);
     if (threadIdx.x == 0) {
         // with more candidates than threads the strided pre-pass may hide a
         // per-thread runner-up: recompute it (n <= blockDim: the merge is exact)
         if (n > (int)blockDim.x) {
             double second = -INFINITY;
-            for (int j = 0; j < n; ++j)
-                if (!chosen[j] && j != b.i1) second = fmax(second, score[j]);
+            for (int c = 0; c < n; ++c)
+                if (!chosen[c] && c != b.i1) second = fmax(second, __ldcg(score + c));
             b.b2 = second;
         }
         if (t == 0) *s0 = b.b1;
@@ -797,6 +805,7 @@ __global__ void __launch_bounds__(256) xray_pick_kernel(const double* __restrict
         K[t] = b.i1;
         if (gap) gap[t] = g;
         chosen[b.i1] = 1;
+        *ticket = 0;
     }
 }
 
@@ -813,11 +822,13 @@ __global__ void xray_res_kernel(const double* __restrict__ R, int n, const int32
     Res[o] = s;
 }
 
-__global__ void init_xray_kernel(const double* __restrict__ R, int n, double* __restrict__ Res, int* __restrict__ chosen)
+__global__ void init_xray_kernel(const double* __restrict__ R, int n, double* __restrict__ Res, int* __restrict__ chosen,
+                                 int* __restrict__ ticket)
 {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o < n * n) Res[o] = R[o];
     if (o < n) chosen[o] = 0;
+    if (o == 0) *ticket = 0;
 }
 
 // ------------------------------------------------------------------------- GP
@@ -1035,12 +1046,11 @@ cudaError_t select_xray(const double* R, int n, int r, int32_t* K, double* gap, 
 {
     if (r > kRMax) return cudaErrorInvalidValue;
     SmallWs w = carve(ws, n, r);
-    init_xray_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(R, n, w.Y, w.chosen);
+    int* ticket = reinterpret_cast<int*>(w.s0 + 1);  // the second half of the 16-byte s0 slot
+    init_xray_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(R, n, w.Y, w.chosen, ticket);
     count_launch();
     for (int t = 0; t < r; ++t) {
-        xray_score_kernel<<<n, 128, 0, s>>>(R, w.Y, n, w.chosen, w.score);
-        count_launch();
-        xray_pick_kernel<<<1, 256, 0, s>>>(w.score, n, t, w.chosen, K, gap, w.s0);
+        xray_score_pick_kernel<<<n, 128, 0, s>>>(R, w.Y, n, w.chosen, w.score, t, K, gap, w.s0, ticket);
         count_launch();
         // warm start from the previous pick's coefficients (same K prefix)
         cudaError_t e = nnls_core(R, n, K, t + 1, w.Hs, w, status, s, t);
