@@ -1052,6 +1052,7 @@ cudaError_t select_xray(const double* R, int n, int r, int32_t* K, double* gap, 
     for (int t = 0; t < r; ++t) {
         xray_score_pick_kernel<<<n, 128, 0, s>>>(R, w.Y, n, w.chosen, w.score, t, K, gap, w.s0, ticket);
         count_launch();
+        if (t + 1 == r) break;  // the residual after the last pick scores nothing
         // warm start from the previous pick's coefficients (same K prefix)
         cudaError_t e = nnls_core(R, n, K, t + 1, w.Hs, w, status, s, t);
         if (e != cudaSuccess) return e;
