@@ -972,19 +972,20 @@ int ctas_per_sm_nc(int n, int k)
 }
 
 // Tile height of the two-column form (32, or 64 when MRNMF_WARP_ROWS=64).
-// Tile height of the one-column form (n <= 32).  Measured on GB300 (4e7
-// rows): 64-row tiles are ~20% faster without the projection at every n
-// and with it from n ~ 29 on; 128-row tiles are ~12% faster with the
-// projection below that.  MRNMF_WARP_ROWS1=64|128 forces one height.
+// Tile height of the one-column form (n <= 32).  Measured on GB300 (1.6e7
+// rows, with the split form for the last 16 columns): 64-row tiles are 3-7%
+// faster than 128-row ones with the projection (n = 16..28) and up to 8%
+// without it.  MRNMF_WARP_ROWS1=64|128 forces one height.
 int rows1(int n, int k)
 {
+    (void)n;
+    (void)k;
     static int forced = [] {
         const char* e = getenv("MRNMF_WARP_ROWS1");
         const int v = e ? atoi(e) : 0;
         return (v == 64 || v == 128) ? v : 0;
     }();
-    if (forced) return forced;
-    return (k <= 0 || n > 28) ? 64 : 128;
+    return forced ? forced : 64;
 }
 
 int rows2()
