@@ -84,6 +84,73 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     }
 }
 
+// Column steps j .. jend-1 in a split form: the 32 / G columns jbase + q are
+// each held by G lanes q + (32 / G) g, lane g owning rows [g L/G, (g+1) L/G)
+// of the tile in a0[0 .. L/G).  Same arithmetic as the one-column steps;
+// the G parts of each dot product are summed by xor shuffles.
+template <int L, int G>
+__device__ __forceinline__ void split_steps(float (&a0)[L], float* Rw, float* pub, int n, int lane, int& j, int jend,
+                                            int jbase)
+{
+    const unsigned FULL = 0xffffffffu;
+    constexpr int QN = 32 / G, LG = L / G;
+    const int g = lane / QN, q = lane % QN;
+    const int cq = jbase + q;
+    const bool oq = cq < n;
+    for (; j < jend; ++j) {
+        const float4* pj = reinterpret_cast<const float4*>(pub + (j & 1) * L + g * LG);
+        const int pr = pk_row(j, n);
+        const float alpha = Rw[pr + j];
+        const float rq = oq ? Rw[pr + cq] : 0.f;
+        constexpr bool kPivReg = LG <= 32;
+        float4 pv[kPivReg ? LG / 4 : 1];
+        float g0a = 0.f, g0b = 0.f, g0c = 0.f, g0d = 0.f;
+#pragma unroll
+        for (int l4 = 0; l4 < LG / 4; ++l4) {
+            const float4 v = pj[l4];
+            if (kPivReg) pv[kPivReg ? l4 : 0] = v;
+            g0a = fmaf(v.x, a0[4 * l4], g0a);
+            g0b = fmaf(v.y, a0[4 * l4 + 1], g0b);
+            g0c = fmaf(v.z, a0[4 * l4 + 2], g0c);
+            g0d = fmaf(v.w, a0[4 * l4 + 3], g0d);
+        }
+        float g0 = (g0a + g0b) + (g0c + g0d);
+#pragma unroll
+        for (int o = QN; o < 32; o <<= 1) g0 += __shfl_xor_sync(FULL, g0, o);
+        const float sig = __shfl_sync(FULL, g0, j - jbase);
+        __syncwarp();
+        float beta = alpha;
+        if (sig > 0.f) {
+            const HhScalars hs = hh_scalars(alpha, sig);
+            beta = hs.beta;
+            const float d = hs.d, rb = hs.rb, rd = hs.rd;
+            float f0 = 0.f;
+            if (oq && cq > j) {
+                const float wp = fmaf(d, rq, g0);
+                f0 = (wp * rd) * rb;
+                if (g == 0) Rw[pr + cq] = fmaf(wp, rb, rq);
+            }
+#pragma unroll
+            for (int l4 = 0; l4 < LG / 4; ++l4) {
+                const float4 v = kPivReg ? pv[kPivReg ? l4 : 0] : pj[l4];
+                a0[4 * l4] = fmaf(f0, v.x, a0[4 * l4]);
+                a0[4 * l4 + 1] = fmaf(f0, v.y, a0[4 * l4 + 1]);
+                a0[4 * l4 + 2] = fmaf(f0, v.z, a0[4 * l4 + 2]);
+                a0[4 * l4 + 3] = fmaf(f0, v.w, a0[4 * l4 + 3]);
+            }
+        }
+        if (lane == j - jbase) Rw[pr + j] = beta;
+        const int jn = j + 1;
+        if (jn < n && q == jn - jbase) {  // every part of the next pivot publishes
+            float4* dst = reinterpret_cast<float4*>(pub + (jn & 1) * L + g * LG);
+#pragma unroll
+            for (int l4 = 0; l4 < LG / 4; ++l4)
+                dst[l4] = make_float4(a0[4 * l4], a0[4 * l4 + 1], a0[4 * l4 + 2], a0[4 * l4 + 3]);
+        }
+        __syncwarp();
+    }
+}
+
 // Householder column steps of the stacked [R; A] for one L-row tile A held in
 // registers (a0: column lane, a1: column lane + 32): R (packed, the warp's
 // shared memory) absorbs A; A is destroyed.  pub is the warp's 2L-float
@@ -245,74 +312,40 @@ __device__ __forceinline__ void column_steps(float (&a0)[L], float (&a1)[NC == 2
         __syncwarp();
     }
     if (j >= n) return;
-    // Split form for the last (at most 16) columns: column jsplit + q is held
-    // by lanes q and q + 16, which own rows [0, L/2) and [L/2, L) of it, so a
-    // step costs half the FMAs; the two halves of each dot product are summed
-    // with one shuffle.  The columns move here from lane (c & 31).
-    constexpr int LH = L / 2;
-    const int hf = lane >> 4, q = lane & 15;
-    const int cq = jsplit + q;
-    const bool oq = cq < n;
+    // Split forms for the last columns: with at most 16 left, column
+    // jsplit + q is held by lanes q and q + 16, each with half of the rows;
+    // with at most 8 left, by lanes q + 8g (g = 0..3), each with a quarter.
+    // A step then costs 1/2 (1/4) of the FMAs and pivot loads, and the parts
+    // of each dot product are summed by xor shuffles.
     {
+        // one column per lane -> halves: column c comes from lane (c & 31)
+        const int hf = lane >> 4, cq = jsplit + (lane & 15);
         const int src = cq & 31;
 #pragma unroll
-        for (int i = 0; i < LH; ++i) {
+        for (int i = 0; i < L / 2; ++i) {
             const float lo = __shfl_sync(FULL, a0[i], src);
-            const float hi = __shfl_sync(FULL, a0[LH + i], src);
+            const float hi = __shfl_sync(FULL, a0[L / 2 + i], src);
             a0[i] = hf ? hi : lo;
         }
     }
-    for (; j < n; ++j) {
-        const float4* pj = reinterpret_cast<const float4*>(pub + (j & 1) * L + hf * LH);
-        const int pr = pk_row(j, n);
-        const float alpha = Rw[pr + j];
-        const float rq = oq ? Rw[pr + cq] : 0.f;
-        constexpr bool kPivReg = LH <= 32;
-        float4 pv[kPivReg ? LH / 4 : 1];
-        float g0a = 0.f, g0b = 0.f, g0c = 0.f, g0d = 0.f;
+    // quarters only pay with at least 16 rows per lane (measured: 2-13% faster
+    // for the 64-row one-column form, 0.5-2% slower for 32-row tiles)
+    const int jq = L < 64 ? n : (n - 8 > jsplit ? n - 8 : jsplit);
+    split_steps<L, 2>(a0, Rw, pub, n, lane, j, jq, jsplit);
+    if (L < 64 || j >= n) return;
+    {
+        // halves -> quarters: rows [gL/4, (g+1)L/4) of column jq + q sit in
+        // half g/2 of that column, at offset (g & 1) L/4
+        const int g = lane >> 3, cq = jq + (lane & 7);
+        const int src = ((cq - jsplit) + 16 * (g >> 1)) & 31;
 #pragma unroll
-        for (int l4 = 0; l4 < LH / 4; ++l4) {
-            const float4 v = pj[l4];
-            if (kPivReg) pv[kPivReg ? l4 : 0] = v;
-            g0a = fmaf(v.x, a0[4 * l4], g0a);
-            g0b = fmaf(v.y, a0[4 * l4 + 1], g0b);
-            g0c = fmaf(v.z, a0[4 * l4 + 2], g0c);
-            g0d = fmaf(v.w, a0[4 * l4 + 3], g0d);
+        for (int i = 0; i < L / 4; ++i) {
+            const float v0 = __shfl_sync(FULL, a0[i], src);
+            const float v1 = __shfl_sync(FULL, a0[L / 4 + i], src);
+            a0[i] = (g & 1) ? v1 : v0;
         }
-        float g0 = (g0a + g0b) + (g0c + g0d);
-        g0 += __shfl_xor_sync(FULL, g0, 16);
-        const float sig = __shfl_sync(FULL, g0, j - jsplit);
-        __syncwarp();
-        float beta = alpha;
-        if (sig > 0.f) {
-            const HhScalars hs = hh_scalars(alpha, sig);
-            beta = hs.beta;
-            const float d = hs.d, rb = hs.rb, rd = hs.rd;
-            float f0 = 0.f;
-            if (oq && cq > j) {
-                const float wp = fmaf(d, rq, g0);
-                f0 = (wp * rd) * rb;
-                if (hf == 0) Rw[pr + cq] = fmaf(wp, rb, rq);
-            }
-#pragma unroll
-            for (int l4 = 0; l4 < LH / 4; ++l4) {
-                const float4 v = kPivReg ? pv[kPivReg ? l4 : 0] : pj[l4];
-                a0[4 * l4] = fmaf(f0, v.x, a0[4 * l4]);
-                a0[4 * l4 + 1] = fmaf(f0, v.y, a0[4 * l4 + 1]);
-                a0[4 * l4 + 2] = fmaf(f0, v.z, a0[4 * l4 + 2]);
-                a0[4 * l4 + 3] = fmaf(f0, v.w, a0[4 * l4 + 3]);
-            }
-        }
-        if (lane == j - jsplit) Rw[pr + j] = beta;
-        const int jn = j + 1;
-        if (jn < n && q == jn - jsplit) {  // both halves of the next pivot publish
-            float4* dst = reinterpret_cast<float4*>(pub + (jn & 1) * L + hf * LH);
-#pragma unroll
-            for (int l4 = 0; l4 < LH / 4; ++l4)
-                dst[l4] = make_float4(a0[4 * l4], a0[4 * l4 + 1], a0[4 * l4 + 2], a0[4 * l4 + 3]);
-        }
-        __syncwarp();
     }
+    split_steps<L, 4>(a0, Rw, pub, n, lane, j, n, jq);
 }
 
 template <int NC, int L, bool GP>
