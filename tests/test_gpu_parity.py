@@ -6,7 +6,7 @@ Tolerances (stated once, used below):
   colsum       : relative 1e-6 (FP32 pass; binary32 tile sums, binary64 across tiles)
   GX           : |GX_gpu - GX_orc| <= 2e-6 * (|G|^T |X|) elementwise, the natural bound of
                  a binary32 sum of products (G drawn in binary32 on the device)
-  H, residual  : relative 1e-4 when K matches (spec bound); 1e-9 on identical inputs
+  H, residual  : relative 1e-4 when K matches; 1e-9 on identical inputs
   K            : bit-exact at every pick whose relative gap exceeds the margin
                  (100x the pass's R error); smaller gaps are tie-ambiguous and only the
                  validity of the pick is checked.

@@ -184,7 +184,7 @@ def test_spa_column_scaling_invariance(oracle):
 def test_spa_bruteforce_unique_subset(oracle):
     # brute force over all r-subsets: exactly one has zero NNLS residual on an
     # exactly separable X, and it is what SPA returns (scipy's NNLS, a
-    # different solver, is the judge of the residual).
+    # different solver, decides the residual).
     from scipy.optimize import nnls as sp_nnls
     n, r = 10, 3
     X, P = synth.planted_separable(200, n, r, seed=26, dtype=np.float64)
