@@ -348,7 +348,8 @@ __global__ void __launch_bounds__(32) nnls_lh_smem_kernel(const double* __restri
 
 
 // ---------------------------------------------------------------------------
-// Lawson-Hanson with one warp per column (r <= 32): lane i holds coefficient i
+// Lawson-Hanson with one warp per column (r <= RM, RM = 16 or 32; the
+// smaller instance halves the unrolled factor code): lane i holds coefficient i
 // (x_i, the dual w_i, passive flag) and, during a solve, row i of the
 // Cholesky factor of the passive block (Lrow) and its column (Lcol).  The
 // steps are the oracle's; every O(p) inner product runs across lanes, so each
@@ -382,6 +383,7 @@ __device__ __forceinline__ double rsqrt_d(double d)
 // memory per block (the same sums, in the same order, as nnls_gram_kernel),
 // and per column A'b = R(:,K)'R(:,c) and b'b = |R(:,c)|^2 (b'b only sets
 // the dual tolerance).
+template <int RM>
 __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restrict__ R,
                                                            const int32_t* __restrict__ K, int r, int n,
                                                            double* __restrict__ H, int r0, int* status)
@@ -426,9 +428,9 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
     // 1/L(k,k); coefficient lane i holds its factor position `my` (or -1).
     // An entering index appends one row (forward substitution, O(p) dependent
     // steps); an index leaving the passive set triggers a full refactor.
-    double Lrow[32], Lcol[32];
+    double Lrow[RM], Lcol[RM];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
+    for (int q = 0; q < RM; ++q) {
         Lrow[q] = 0.0;
         Lcol[q] = 0.0;
     }
@@ -446,7 +448,7 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
         }
         const bool in = lane < p;
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
+        for (int q = 0; q < RM; ++q) {
             Lrow[q] = 0.0;
             Lcol[q] = 0.0;
         }
@@ -454,14 +456,14 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
         bool ok = true;
         // right-looking Cholesky of AtA[idx, idx]
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
+        for (int k = 0; k < RM; ++k) {
             if (k >= p) break;
             const int ik = __shfl_sync(FULL, idx, k);
             double d = 0.0;
             if (lane == k) {
                 d = AtA[idx * r + idx];
 #pragma unroll
-                for (int q = 0; q < 32; ++q)
+                for (int q = 0; q < RM; ++q)
                     if (q < k) d -= Lrow[q] * Lrow[q];
             }
             d = shfl_d(d, k);
@@ -474,7 +476,7 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
             // L(a,k) for a > k: (A(a,k) - sum_{q<k} L(a,q) L(k,q)) / L(k,k)
             double s = (in && lane > k) ? AtA[idx * r + ik] : 0.0;
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
+            for (int q = 0; q < RM; ++q) {
                 if (q < k) {
                     const double lkq = shfl_d(Lrow[q], k);
                     s -= Lrow[q] * lkq;
@@ -484,7 +486,7 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
             if (in && lane > k) Lrow[k] = lak;
             // lane k collects its column: L(a,k) for a > k
 #pragma unroll
-            for (int a = 0; a < 32; ++a) {
+            for (int a = 0; a < RM; ++a) {
                 if (a > k && a < p) {
                     const double v = shfl_d(lak, a);
                     if (lane == k) Lcol[a] = v;
@@ -500,7 +502,7 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
         double b = lane < p ? AtA[idx * r + bi] : 0.0;
         double l = 0.0;
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
+        for (int q = 0; q < RM; ++q) {
             if (q >= p) break;
             if (lane == q) l = b * invd;
             const double lq = shfl_d(l, q);
@@ -516,12 +518,12 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
             invd = ik_inv;
             idx = bi;
 #pragma unroll
-            for (int q = 0; q < 32; ++q)
+            for (int q = 0; q < RM; ++q)
                 if (q >= p) Lrow[q] = 0.0;
         }
         if (lane < p) {
 #pragma unroll
-            for (int a = 0; a < 32; ++a)
+            for (int a = 0; a < RM; ++a)
                 if (a == p) Lcol[a] = l;
         }
         if (lane == bi) my = p;
@@ -538,7 +540,7 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
             const double bk = shfl_d(rhs, idx);  // lane k: rhs of its passive index (lanes >= p: junk, unused)
             double acc = 0.0, y = 0.0;
     #pragma unroll
-            for (int k = 0; k < 32; ++k) {
+            for (int k = 0; k < RM; ++k) {
                 if (k >= p) break;
                 double yk = 0.0;
                 if (lane == k) {
@@ -552,7 +554,7 @@ __global__ void __launch_bounds__(128) nnls_lh_warp_kernel(const double* __restr
             double z = 0.0;
             double acc2 = 0.0;
     #pragma unroll
-            for (int k = 31; k >= 0; --k) {
+            for (int k = RM - 1; k >= 0; --k) {
                 if (k >= p) continue;
                 double zk = 0.0;
                 if (lane == k) {
@@ -741,21 +743,29 @@ __global__ void __launch_bounds__(128) xray_score_pick_kernel(const double* __re
 {
     __shared__ double sh[8];
     __shared__ Top2 sht[8];
+    __shared__ double rj[MRNMF_NMAX];
     __shared__ int last;
     const int j = blockIdx.x;
     if (!chosen[j]) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) rj[i] = R[(size_t)i * n + j];
+        __syncthreads();
         double acc = 0.0, cn = 0.0;
         for (int q = threadIdx.x; q < n; q += blockDim.x) {
-            double v = 0.0;
-#pragma unroll 8  // keep eight loads in flight: each is an L2 round trip
-            for (int i = 0; i < n; ++i) v += Res[(size_t)i * n + q] * R[(size_t)i * n + j];
+            // four partial sums: the binary64 chain is the latency of this kernel
+            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+            int i = 0;
+            for (; i + 4 <= n; i += 4) {
+                v0 = fma(Res[(size_t)i * n + q], rj[i], v0);
+                v1 = fma(Res[(size_t)(i + 1) * n + q], rj[i + 1], v1);
+                v2 = fma(Res[(size_t)(i + 2) * n + q], rj[i + 2], v2);
+                v3 = fma(Res[(size_t)(i + 3) * n + q], rj[i + 3], v3);
+            }
+            for (; i < n; ++i) v0 = fma(Res[(size_t)i * n + q], rj[i], v0);
+            const double v = (v0 + v1) + (v2 + v3);
             acc += v * v;
         }
         if (threadIdx.x < 32) {
-            for (int i = threadIdx.x; i < n; i += 32) {
-                const double x = R[(size_t)i * n + j];
-                cn += x * x;
-            }
+            for (int i = threadIdx.x; i < n; i += 32) cn += rj[i] * rj[i];
             cn = warp_sum(cn);
         }
         acc = warp_sum(acc);
@@ -975,7 +985,10 @@ cudaError_t nnls_core(const double* R, int n, const int32_t* K, int r, double* H
                       cudaStream_t s, int r0 = 0)
 {
     if (r <= 32) {
-        nnls_lh_warp_kernel<<<(n + 3) / 4, 128, 0, s>>>(R, K, r, n, H, r0, status);
+        if (r <= 16)
+            nnls_lh_warp_kernel<16><<<(n + 3) / 4, 128, 0, s>>>(R, K, r, n, H, r0, status);
+        else
+            nnls_lh_warp_kernel<32><<<(n + 3) / 4, 128, 0, s>>>(R, K, r, n, H, r0, status);
         count_launch();
         return cudaGetLastError();
     }
