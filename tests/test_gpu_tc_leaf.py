@@ -145,8 +145,10 @@ def test_tf32x3_bad_input_is_reported(h):
 
 
 def test_tf32x3_rejects_unsupported_shape(h):
+    # the tensor-core form covers 16 < n <= 64 (k <= 32)
     from paper_1402_6964_gb300 import mrnmf
-    X = synth.random_nonneg(1000, 10, seed=2)
-    with pytest.raises(mrnmf.MrnmfError) as e:
-        h.tsqr_r(dev(X), prec="tf32x3")
-    assert e.value.status == mrnmf.ERR_INVALID_ARG
+    for m, n in [(1000, 10), (1000, 200)]:
+        X = synth.random_nonneg(m, n, seed=2)
+        with pytest.raises(mrnmf.MrnmfError) as e:
+            h.tsqr_r(dev(X), prec="tf32x3")
+        assert e.value.status == mrnmf.ERR_INVALID_ARG
