@@ -147,7 +147,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": w.name, "m": w.m, "n": w.n, "r": w.r, "k": w.k, "parallelism": "replicas"},
+            "config": {"workload": w.name, "m": w.m, "n": w.n, "r": w.r, "k": w.k, "prec": args.prec,
+                       "parallelism": "replicas" if args.gpus > 1 else "single GPU"},
             "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": f"first {rows} rows of the {w.m}-row workload per step"},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

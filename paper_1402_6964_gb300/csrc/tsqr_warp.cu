@@ -18,6 +18,8 @@
 // beta and alpha - beta, since tau s = -1/beta).  The owner of column j+1 then
 // publishes its updated column.  One warp barrier per column, no block
 // barriers, no cross-lane reductions except the broadcast of sigma.
+// Once at most 16 (8) columns of a tile remain, two (four) lanes share each
+// column by rows, and xor shuffles sum the parts of its dot products.
 //
 // Column sums and the Gaussian projection (Algorithm 1, with the combiner of
 // Sec. 3.2) are folded into the same pass: binary32 per tile, binary64 across
@@ -35,7 +37,7 @@ namespace {
 constexpr int kWarps = 4;  // streams per CTA
 constexpr int kFlush = 32;  // tiles between binary64 flushes of the partial sums
 
-// Tile heights: 128 rows when a lane owns one column (n <= 32), 32 rows when
+// Tile heights: 64 rows when a lane owns one column (n <= 32), 32 rows when
 // it owns two (n <= 64): three 4-warp CTAs then fit per SM (measured faster
 // on GB300 than 64-row tiles with two CTAs; MRNMF_WARP_ROWS=64 selects those).
 
