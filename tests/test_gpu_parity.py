@@ -113,6 +113,24 @@ def test_tsqr_ill_conditioned(h, oracle):
     assert np.max(col) < 1e-3
 
 
+def test_fused_ill_conditioned_n200(h, oracle):
+    # the 1e8 x 200 workload's recipe (r = 20, 10^U(0,6) column scaling, k = 40)
+    # at 60,000 rows, through the pipelined leaf and the fan-in-2 tree: R, the
+    # column sums and GX against the oracle on the same rows
+    X, P = synth.planted_separable(60000, 200, 20, seed=1402002, noise=1e-3, decades=6.0)
+    R, cs, GX = h.tsqr_gp(dev(X), 40, seed=1402002)
+    h.sync()
+    X64 = X.astype(np.float64)
+    Ro = oracle.qr_r(X64)
+    Rg = host(R)
+    assert rel_fro(Rg, Ro) <= R_TOL_FP32
+    col = np.linalg.norm(Rg - Ro, axis=0) / np.linalg.norm(Ro, axis=0)
+    assert np.max(col) < 1e-3
+    np.testing.assert_allclose(host(cs), oracle.colsum(X64), rtol=1e-6)
+    GXo = oracle.gauss_project(X64, 40, 1402002)
+    assert np.all(np.abs(host(GX) - GXo) <= 2e-6 * _gx_bound(X, 40, 1402002) + 1e-12)
+
+
 def test_bad_input_is_reported(h):
     from paper_1402_6964_gb300 import mrnmf
     X = synth.random_nonneg(500, 6, seed=1)
