@@ -63,3 +63,25 @@ def test_reference_arm_runs_on_rank_zero_only():
                          timeout=300)
     assert out.returncode == 0
     assert out.stdout.strip() == ""
+
+
+def test_reference_arm_line_contract():
+    # rank 0 prints one JSON line with the reference arm's keys: the oracle on
+    # a bounded sample of the same workload, no host-device traffic
+    import json
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "1", "--ref-rows", "2000"], env=env, capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    b = json.loads(lines[0])
+    sys.path.insert(0, ROOT)
+    import bench
+    assert b["impl"] == "reference" and b["metric"] == bench.METRIC and b["unit"] == "GB/s"
+    assert b["value"] > 0 and b["higher_is_better"] is True and b["steps"] == 1
+    assert b["cpu_baseline"]["kind"] == "oracle" and b["cpu_baseline"]["cores"] >= 1
+    assert b["cpu_baseline"]["value"] == b["value"]
+    assert b["e2e"] == {"value": b["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert b["config"]["workload"] and b["config"]["parallelism"] == "single GPU"
