@@ -229,6 +229,45 @@ def test_xray_on_R_equals_xray_on_X(oracle):
     assert list(KX) == list(KR)
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_xray_every_pick_is_the_scores_argmax(oracle, seed):
+    # Sec. 2.1: after each pick, Res = X - X(:,K)H with H the NNLS fit of every
+    # column (scipy's active-set NNLS here, a separate solver), and the next
+    # pick maximises ||Res^T x_j|| / ||x_j|| over the unchosen columns
+    from scipy.optimize import nnls as sp_nnls
+    X, P = synth.planted_separable(400, 12, 5, seed=40 + seed, noise=1e-2, dtype=np.float64)
+    r = 5
+    K, gap, st = oracle.xray(X, r)
+    assert st == 0
+    chosen = []
+    Res = X.copy()
+    for t in range(r):
+        scores = np.linalg.norm(Res.T @ X, axis=0) / np.linalg.norm(X, axis=0)
+        scores[chosen] = -np.inf
+        order = np.argsort(-scores, kind="stable")
+        best, second = scores[order[0]], scores[order[1]]
+        if (best - second) / best > 1e-9:  # clear pick: the rule fixes it
+            assert K[t] == order[0], (t, K, order[:3])
+        chosen.append(int(K[t]))
+        A = X[:, chosen]
+        H = np.stack([sp_nnls(A, X[:, c])[0] for c in range(X.shape[1])], axis=1)
+        Res = X - A @ H
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_nnls_matches_scipy_for_larger_r(oracle, seed):
+    # beyond brute-force sizes: the minimiser is unique (full column rank), so
+    # it equals scipy's active-set NNLS solution
+    from scipy.optimize import nnls as sp_nnls
+    g = np.random.default_rng(200 + seed)
+    m, r = 60, 24
+    A = g.standard_normal((m, r))
+    b = g.standard_normal(m)
+    x, st = oracle.nnls(A.T @ A, A.T @ b, b @ b)
+    assert st == 0
+    np.testing.assert_allclose(x, sp_nnls(A, b)[0], rtol=1e-8, atol=1e-10)
+
+
 # -------------------------------------------------------------- GP (Sec. 2.3)
 
 def test_gp_hand(oracle):
