@@ -11,6 +11,7 @@ Each wrapper names the passage of Benson, Lee, Rajwa and Gleich (arXiv
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -40,28 +41,47 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _bind(lib):
+    d, i64, i32, u64 = ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64
+    P = ctypes.c_void_p
+    lib.orc_qr_r.argtypes = [P, i64, i64, i32, P]
+    lib.orc_colsum.argtypes = [P, i64, i64, i32, P]
+    lib.orc_philox4x32_10.argtypes = [P, P, P]
+    lib.orc_gauss_entry.argtypes = [u64, i64, i32]
+    lib.orc_gauss_entry.restype = d
+    lib.orc_gauss_matrix.argtypes = [u64, i64, i64, i32, P]
+    lib.orc_gauss_project.argtypes = [P, i64, i64, i32, i32, u64, i64, P]
+    lib.orc_nnls.argtypes = [P, P, d, i32, P]
+    lib.orc_nnls_h.argtypes = [P, i32, i32, P, i32, P]
+    lib.orc_residual.argtypes = [P, i32, i32, P, i32, P, P]
+    lib.orc_spa.argtypes = [P, i32, i32, P, i32, P, P]
+    lib.orc_xray.argtypes = [P, i32, i32, i32, P, P]
+    lib.orc_gp_select.argtypes = [P, i32, i32, P, i32, P, P, P, P, P]
+    return lib
+
+
+@contextlib.contextmanager
+def substituted(path: str):
+    """Route every wrapper to another build of the oracle's source (the pin
+    tests use this to check that a planted mistake fails a pin)."""
+    global _lib
+    lib = _bind(ctypes.CDLL(path))
+    with _lock:
+        saved = _lib
+        _lib = lib
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = saved
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_LIB)
-            d, i64, i32, u64 = ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64
-            P = ctypes.c_void_p
-            lib.orc_qr_r.argtypes = [P, i64, i64, i32, P]
-            lib.orc_colsum.argtypes = [P, i64, i64, i32, P]
-            lib.orc_philox4x32_10.argtypes = [P, P, P]
-            lib.orc_gauss_entry.argtypes = [u64, i64, i32]
-            lib.orc_gauss_entry.restype = d
-            lib.orc_gauss_matrix.argtypes = [u64, i64, i64, i32, P]
-            lib.orc_gauss_project.argtypes = [P, i64, i64, i32, i32, u64, i64, P]
-            lib.orc_nnls.argtypes = [P, P, d, i32, P]
-            lib.orc_nnls_h.argtypes = [P, i32, i32, P, i32, P]
-            lib.orc_residual.argtypes = [P, i32, i32, P, i32, P, P]
-            lib.orc_spa.argtypes = [P, i32, i32, P, i32, P, P]
-            lib.orc_xray.argtypes = [P, i32, i32, i32, P, P]
-            lib.orc_gp_select.argtypes = [P, i32, i32, P, i32, P, P, P, P, P]
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(_LIB))
     return _lib
 
 
