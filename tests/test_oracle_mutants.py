@@ -138,6 +138,23 @@ def pin_xray_first_pick(orc):
     return K[0] == int(np.argmax(scores))
 
 
+def pin_xray_scores(orc):
+    from scipy.optimize import nnls as sp_nnls
+    X, P = synth.planted_separable(400, 12, 5, seed=40, noise=1e-2, dtype=np.float64)
+    K, gap, st = orc.xray(X, 5)
+    chosen, Res = [], X.copy()
+    for t in range(5):
+        scores = np.linalg.norm(Res.T @ X, axis=0) / np.linalg.norm(X, axis=0)
+        scores[chosen] = -np.inf
+        order = np.argsort(-scores, kind="stable")
+        if (scores[order[0]] - scores[order[1]]) / scores[order[0]] > 1e-9 and K[t] != order[0]:
+            return False
+        chosen.append(int(K[t]))
+        A = X[:, chosen]
+        Res = X - A @ np.stack([sp_nnls(A, X[:, c])[0] for c in range(X.shape[1])], axis=1)
+    return st == 0
+
+
 def pin_residual_full(orc):
     X, P = synth.planted_separable(2500, 16, 5, seed=32, noise=1e-2, dtype=np.float64)
     R = orc.qr_r(X)
@@ -154,7 +171,7 @@ def pin_gp_hand(orc):
 
 
 PINS = [pin_qr_gram, pin_qr_cholesky, pin_colsum_exact, pin_philox_kat, pin_gauss_moments, pin_gx_matmul,
-        pin_nnls_brute, pin_nnls_scipy, pin_spa_hand, pin_xray_hand, pin_xray_first_pick, pin_residual_full, pin_gp_hand]
+        pin_nnls_brute, pin_nnls_scipy, pin_spa_hand, pin_xray_hand, pin_xray_first_pick, pin_xray_scores, pin_residual_full, pin_gp_hand]
 
 # ---------------------------------------------------------------- the mistakes
 
@@ -184,6 +201,11 @@ MUTANTS = {
         "Y[(int64_t)i * n + j] = Y0[(int64_t)i * n + j];"),
     "xray: score not divided by the column norm": (
         "score[j] = cn[j] > 0.0 ? sqrt(s) / cn[j] : 0.0;", "score[j] = sqrt(s);"),
+    "xray: residual not refreshed after a pick": (
+        "Res[(int64_t)i * n + c] = s;", "Res[(int64_t)i * n + c] = Y0[(int64_t)i * n + c];"),
+    "xray: newest pick left out of the residual": (
+        "for (int a = 0; a <= t; ++a) s -= Y0[(int64_t)i * n + K[a]] * H[(int64_t)a * n + c];",
+        "for (int a = 0; a < t; ++a) s -= Y0[(int64_t)i * n + K[a]] * H[(int64_t)a * n + c];"),
     "residual: wrong term in the denominator": (
         "r2 += v * v;", "r2 += s * s;"),
     "gp: min before max": (
