@@ -8,7 +8,7 @@ Metric: GB/s of X read per step (4 m n bytes / step time).
 
 Multi-GPU (torchrun): the pass has no exchange step on one box, so every rank
 runs an independent replica on its own GPU; value = bytes all ranks read /
-max over ranks of the timed wall time ("scaling": "weak").
+max over ranks of the timed region (CUDA events) ("scaling": "weak").
 
 --impl reference times the FP64 CPU oracle (the only reference this project
 has) on the host cores on a bounded row sample of the same workload.
