@@ -240,9 +240,10 @@ mrnmf_status mrnmf_stream_state_load(mrnmf_handle* handle, const void* host, siz
  * Batched pass: R (and colsum) of many independent problems of uneven m and n
  * (Sec. 3.1's TSQR applied to each), FP32 form, enqueued on `stream` as a
  * handful of launches for the whole batch: the row streams of all problems
- * with n <= 64 share one leaf launch per tile shape, their trees one launch
- * per level, and one launch writes every R and colsum; problems with n > 64
- * run the one-problem pass in turn.  Each problem's share of the streams is
+ * with n <= 128 share one leaf launch per family (n <= 32, 33..64 and
+ * 65..128), their trees one launch per level, and one launch writes every R
+ * and colsum; problems with n > 128 run the one-problem pass in turn.  Each
+ * problem's share of the streams is
  * planned on the host from its m and n (cost-balanced), tile height and tree
  * fan-in follow n.
  *   problems  host array of `count` descriptors (device X, R, colsum):
