@@ -59,7 +59,7 @@ typedef enum { MRNMF_F32 = 0, MRNMF_F64 = 1 } mrnmf_dtype;
  * k <= 32, else MRNMF_ERR_INVALID_ARG): binary32 reflectors in 16-column
  * panels with the compact-WY trailing update and the Gaussian projection on
  * tcgen05 tensor cores in 3-pass split TF32 (hi*hi + hi*lo + lo*hi), FP32
- * accumulation; R within 1e-5 of the FP64 oracle but about 30x the FP32
+ * accumulation; R within 1e-5 of the FP64 oracle but about 50x the FP32
  * form's error, and slower than FP32 on GB300, so AUTO does not pick it.
  * AUTO picks FP64 for F64 input, otherwise FP32. */
 typedef enum { MRNMF_PREC_AUTO = 0, MRNMF_PREC_FP64 = 1, MRNMF_PREC_FP32 = 2, MRNMF_PREC_TF32X3 = 3 } mrnmf_prec;
