@@ -150,7 +150,7 @@ def run_reference(args):
             "config": {"workload": w.name, "m": w.m, "n": w.n, "r": w.r, "k": w.k, "prec": args.prec,
                        "parallelism": "replicas" if args.gpus > 1 else "single GPU"},
             "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {rows} rows of the {w.m}-row workload per step"},
+                             "sample": f"{rows} rows per step, drawn by the {w.m}-row workload's generator"},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -25,3 +25,39 @@ def test_kron_planted_columns_generate_the_rest():
     assert rank == 16
     assert np.linalg.norm(X[:, K] @ H - X) <= 1e-10 * np.linalg.norm(X)
     assert len(K) == 16 and len(set(K.tolist())) == 16
+
+
+def test_planted_structure_is_separable():
+    # X = W [I H'] Pi (Sec. 4's generator): X(:,K) H_true = X exactly without
+    # noise, the columns of H' lie in the simplex, and the scaling moves with
+    # the permutation
+    X, P = synth.planted_separable(3000, 20, 6, seed=5, dtype=np.float64, decades=3.0)
+    assert len(P.K) == 6 and np.all(np.diff(P.K) > 0)
+    np.testing.assert_allclose(X[:, P.K] @ P.H_true, X, rtol=1e-12, atol=1e-12)
+    Hp = P.Hmix / P.colscale[None, :]
+    others = np.setdiff1d(np.arange(20), P.K)
+    np.testing.assert_allclose(Hp[:, others].sum(0), 1.0, rtol=1e-12)
+    assert np.all(Hp >= 0)
+    assert np.all((P.colscale >= 1.0) & (P.colscale <= 1e3))
+
+
+def test_whole_chunks_regenerate_alone():
+    # chunk c is drawn from (seed, c) alone: the whole chunks of a longer X are
+    # those of a shorter one, and a chunk can be regenerated by itself
+    X, P = synth.planted_separable(3 * synth.CHUNK_ROWS // 2, 10, 4, seed=9, noise=1e-3)
+    Xs, _ = synth.planted_separable(synth.CHUNK_ROWS + 100, 10, 4, seed=9, noise=1e-3)
+    assert np.array_equal(X[:synth.CHUNK_ROWS], Xs[:synth.CHUNK_ROWS])
+    c1 = synth.rows_chunk(P, 9, 1, synth.CHUNK_ROWS // 2, noise=1e-3)
+    assert np.array_equal(c1, X[synth.CHUNK_ROWS:])
+    assert np.all(X >= 0)
+
+
+def test_batch_shapes_follow_their_recipe():
+    probs = synth.batch_problems(256, seed=3)
+    m = np.array([p[0] for p in probs])
+    n = np.array([p[1] for p in probs])
+    r = np.array([p[2] for p in probs])
+    assert np.all((m >= 1e4 - 1) & (m <= 1e7 + 1)) and np.all((n >= 10) & (n <= 128))
+    assert np.all((r >= 3) & (r <= np.maximum(3, np.minimum(16, n // 2))))
+    # log-uniform m: the median is near the geometric mean of the range
+    assert 1e5 < np.median(m) < 1e6
