@@ -13,6 +13,7 @@
 
 #include "../../include/mrnmf.h"
 #include "internal.h"
+#include "trace.h"
 #include "handle.h"
 #include "leaf.h"
 
@@ -181,6 +182,7 @@ const char* mrnmf_last_error_string(const mrnmf_handle* h)
 
 mrnmf_status mrnmf_sync_status(mrnmf_handle* h, void* stream)
 {
+    MRNMF_TRACE("mrnmf_sync_status");
     if (!h) return MRNMF_ERR_INVALID_ARG;
     if (h->device < 0) return MRNMF_OK;
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
@@ -204,6 +206,7 @@ mrnmf_status mrnmf_sync_status(mrnmf_handle* h, void* stream)
 mrnmf_status mrnmf_tsqr_r(mrnmf_handle* h, const void* X, int64_t m, int32_t n, int64_t ldx, int32_t dtype,
                           int32_t prec, double* R, double* colsum, void* stream)
 {
+    MRNMF_TRACE("mrnmf_tsqr_r");
     mrnmf_status s = check_pass_args(h, X, m, n, ldx, dtype, prec, 0);
     if (s != MRNMF_OK) return s;
     if (!R) return fail(h, MRNMF_ERR_INVALID_ARG, "R is NULL");
@@ -215,6 +218,7 @@ mrnmf_status mrnmf_gauss_project(mrnmf_handle* h, const void* X, int64_t m, int3
                                  int32_t k, uint64_t seed, int64_t row_offset, double* GX, double* colsum,
                                  void* stream)
 {
+    MRNMF_TRACE("mrnmf_gauss_project");
     mrnmf_status s = check_pass_args(h, X, m, n, ldx, dtype, MRNMF_PREC_AUTO, k);
     if (s != MRNMF_OK) return s;
     if (k < 1 || !GX) return fail(h, MRNMF_ERR_INVALID_ARG, "need k >= 1 and GX");
@@ -229,6 +233,7 @@ mrnmf_status mrnmf_tsqr_gp(mrnmf_handle* h, const void* X, int64_t m, int32_t n,
                            int32_t prec, double* R, double* colsum, int32_t k, uint64_t seed, double* GX,
                            void* stream)
 {
+    MRNMF_TRACE("mrnmf_tsqr_gp");
     mrnmf_status s = check_pass_args(h, X, m, n, ldx, dtype, prec, k);
     if (s != MRNMF_OK) return s;
     if (!R) return fail(h, MRNMF_ERR_INVALID_ARG, "R is NULL");
@@ -241,6 +246,7 @@ mrnmf_status mrnmf_tsqr_gp(mrnmf_handle* h, const void* X, int64_t m, int32_t n,
 mrnmf_status mrnmf_select_extreme(mrnmf_handle* h, int32_t method, const double* R, int32_t n, const double* colsum,
                                   const double* GX, int32_t k, int32_t r, int32_t* K, double* gap, void* stream)
 {
+    MRNMF_TRACE("mrnmf_select_extreme");
     if (!h) return MRNMF_ERR_INVALID_ARG;
     if (n < 1 || n > MRNMF_NMAX) return fail(h, MRNMF_ERR_INVALID_ARG, "n must be in [1, 256]");
     if (r < 1 || r > n) return fail(h, MRNMF_ERR_INVALID_ARG, "need 1 <= r <= n");
@@ -272,6 +278,7 @@ mrnmf_status mrnmf_select_extreme(mrnmf_handle* h, int32_t method, const double*
 mrnmf_status mrnmf_nnls_h(mrnmf_handle* h, const double* R, int32_t n, const int32_t* K, int32_t r, double* H,
                           void* stream)
 {
+    MRNMF_TRACE("mrnmf_nnls_h");
     if (!h) return MRNMF_ERR_INVALID_ARG;
     if (!R || !K || !H) return fail(h, MRNMF_ERR_INVALID_ARG, "NULL argument");
     if (n < 1 || n > MRNMF_NMAX || r < 1 || r > n || r > 64)
@@ -288,6 +295,7 @@ mrnmf_status mrnmf_nnls_h(mrnmf_handle* h, const double* R, int32_t n, const int
 mrnmf_status mrnmf_residual(mrnmf_handle* h, const double* R, int32_t n, const int32_t* K, int32_t r, const double* H,
                             double* out, void* stream)
 {
+    MRNMF_TRACE("mrnmf_residual");
     if (!h) return MRNMF_ERR_INVALID_ARG;
     if (!R || !K || !H || !out) return fail(h, MRNMF_ERR_INVALID_ARG, "NULL argument");
     if (n < 1 || n > MRNMF_NMAX || r < 1 || r > n) return fail(h, MRNMF_ERR_INVALID_ARG, "need 1 <= r <= n <= 256");
@@ -303,6 +311,7 @@ mrnmf_status mrnmf_residual(mrnmf_handle* h, const double* R, int32_t n, const i
 mrnmf_status mrnmf_rank_sweep(mrnmf_handle* h, int32_t method, const double* R, int32_t n, const double* colsum,
                               const double* GX, int32_t k, int32_t r_max, int32_t* K, double* curve, void* stream)
 {
+    MRNMF_TRACE("mrnmf_rank_sweep");
     if (!h) return MRNMF_ERR_INVALID_ARG;
     if (!R || !K || !curve) return fail(h, MRNMF_ERR_INVALID_ARG, "R, K and curve are required");
     if (n < 1 || n > MRNMF_NMAX || r_max < 1 || r_max > n || r_max > 64)
@@ -321,6 +330,7 @@ mrnmf_status mrnmf_rank_sweep(mrnmf_handle* h, int32_t method, const double* R, 
 mrnmf_status mrnmf_stream_begin(mrnmf_handle* h, int32_t n, int32_t dtype, int32_t prec, int32_t k, uint64_t seed,
                                 void* stream)
 {
+    MRNMF_TRACE("mrnmf_stream_begin");
     if (!h) return MRNMF_ERR_INVALID_ARG;
     if (n < 1 || n > MRNMF_NMAX) return fail(h, MRNMF_ERR_INVALID_ARG, "n must be in [1, 256]");
     if (dtype != MRNMF_F32 && dtype != MRNMF_F64) return fail(h, MRNMF_ERR_INVALID_ARG, "bad dtype");
@@ -338,6 +348,7 @@ mrnmf_status mrnmf_stream_begin(mrnmf_handle* h, int32_t n, int32_t dtype, int32
 
 mrnmf_status mrnmf_stream_push(mrnmf_handle* h, const void* X_chunk, int64_t rows, int64_t ldx, void* stream)
 {
+    MRNMF_TRACE("mrnmf_stream_push");
     if (!h) return MRNMF_ERR_INVALID_ARG;
     if (!h->open) return fail(h, MRNMF_ERR_INVALID_ARG, "no open stream (call mrnmf_stream_begin)");
     if (rows < 0 || (rows > 0 && !X_chunk) || ldx < h->st.n) return fail(h, MRNMF_ERR_INVALID_ARG, "bad chunk");
@@ -383,6 +394,7 @@ mrnmf_status mrnmf_stream_state_size(mrnmf_handle* h, size_t* bytes)
 
 mrnmf_status mrnmf_stream_state_save(mrnmf_handle* h, void* host, size_t bytes, void* stream)
 {
+    MRNMF_TRACE("mrnmf_stream_state_save");
     if (!h || !host) return MRNMF_ERR_INVALID_ARG;
     if (!h->open) return fail(h, MRNMF_ERR_INVALID_ARG, "no open stream");
     size_t need = 0;
@@ -416,6 +428,7 @@ mrnmf_status mrnmf_stream_state_save(mrnmf_handle* h, void* host, size_t bytes, 
 
 mrnmf_status mrnmf_stream_state_load(mrnmf_handle* h, const void* host, size_t bytes, void* stream)
 {
+    MRNMF_TRACE("mrnmf_stream_state_load");
     if (!h || !host) return MRNMF_ERR_INVALID_ARG;
     if (!h->open) return fail(h, MRNMF_ERR_INVALID_ARG, "no open stream (begin one with the saved parameters)");
     if (bytes < sizeof(StreamStateHeader)) return fail(h, MRNMF_ERR_INVALID_ARG, "state buffer too small");
@@ -445,6 +458,7 @@ mrnmf_status mrnmf_stream_state_load(mrnmf_handle* h, const void* host, size_t b
 
 mrnmf_status mrnmf_stream_end(mrnmf_handle* h, double* R, double* colsum, double* GX, void* stream)
 {
+    MRNMF_TRACE("mrnmf_stream_end");
     if (!h) return MRNMF_ERR_INVALID_ARG;
     if (!h->open) return fail(h, MRNMF_ERR_INVALID_ARG, "no open stream");
     if (!R) return fail(h, MRNMF_ERR_INVALID_ARG, "R is NULL");
@@ -462,6 +476,7 @@ mrnmf_status mrnmf_factorize_host(mrnmf_handle* h, const float* X, int64_t m, in
                                   int32_t method, int32_t r, int32_t k, uint64_t seed, int32_t* K, double* H,
                                   double* resid, double* R, void* stream)
 {
+    MRNMF_TRACE("mrnmf_factorize_host");
     mrnmf_status s = check_pass_args(h, X, m, n, ldx, MRNMF_F32, prec, method == MRNMF_GP ? k : 0);
     if (s != MRNMF_OK) return s;
     if (!K || !H || !resid) return fail(h, MRNMF_ERR_INVALID_ARG, "K, H and resid are required");

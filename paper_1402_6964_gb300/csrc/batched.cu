@@ -28,6 +28,7 @@
 #include "common.cuh"
 #include "handle.h"
 #include "internal.h"
+#include "trace.h"
 #include "leaf.h"
 
 namespace mrnmf {
@@ -293,6 +294,7 @@ using namespace mrnmf::api;
 
 extern "C" mrnmf_status mrnmf_tsqr_r_batched(mrnmf_handle* h, const mrnmf_problem* pr, int32_t count, void* stream)
 {
+    MRNMF_TRACE("mrnmf_tsqr_r_batched");
     if (!h) return MRNMF_ERR_INVALID_ARG;
     if (!pr || count < 1) return fail(h, MRNMF_ERR_INVALID_ARG, "need count >= 1 problems");
     for (int i = 0; i < count; ++i) {

@@ -10,6 +10,7 @@
 #include "common.cuh"
 #include "handle.h"
 #include "internal.h"
+#include "trace.h"
 
 namespace mrnmf {
 namespace {
@@ -193,6 +194,7 @@ extern "C" mrnmf_status mrnmf_gather_columns(mrnmf_handle* h, const void* X, int
                                              int32_t dtype, const int32_t* K, int32_t r, void* W, int64_t ldw,
                                              void* stream)
 {
+    MRNMF_TRACE("mrnmf_gather_columns");
     if (!h) return MRNMF_ERR_INVALID_ARG;
     if (!X || !K || !W) return fail(h, MRNMF_ERR_INVALID_ARG, "NULL argument");
     if (n < 1 || m < 1 || ldx < n || r < 1 || r > n || ldw < r)
@@ -217,6 +219,7 @@ extern "C" mrnmf_status mrnmf_full_residual(mrnmf_handle* h, const void* X, int6
                                             int32_t dtype, const int32_t* K, int32_t r, const double* H, double* out,
                                             void* stream)
 {
+    MRNMF_TRACE("mrnmf_full_residual");
     if (!h) return MRNMF_ERR_INVALID_ARG;
     if (!X || !K || !H || !out) return fail(h, MRNMF_ERR_INVALID_ARG, "NULL argument");
     if (n < 1 || n > MRNMF_NMAX || m < 1 || ldx < n || r < 1 || r > n)

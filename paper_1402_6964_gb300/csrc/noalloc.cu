@@ -27,6 +27,7 @@
 
 #include "../../include/mrnmf.h"
 #include "internal.h"
+#include "trace.h"
 
 namespace {
 
@@ -62,6 +63,7 @@ cudaError_t scratch_address(void** out)
 extern "C" mrnmf_status mrnmf_tsqr_r_noalloc(const float* X, int64_t m, int32_t n, int64_t ldx, double* R,
                                              double* colsum, int32_t* status, void* stream)
 {
+    MRNMF_TRACE("mrnmf_tsqr_r_noalloc");
     if (!X || !R) return MRNMF_ERR_INVALID_ARG;
     if (n < 1 || n > MRNMF_NMAX || m < n || ldx < n) return MRNMF_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

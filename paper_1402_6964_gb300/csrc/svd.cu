@@ -22,6 +22,7 @@
 #include "common.cuh"
 #include "handle.h"
 #include "internal.h"
+#include "trace.h"
 
 namespace mrnmf {
 namespace {
@@ -143,6 +144,7 @@ using mrnmf::api::grow;
 extern "C" mrnmf_status mrnmf_r_svd(mrnmf_handle* h, const double* R, int32_t n, double* sigma, double* SVt,
                                     void* stream)
 {
+    MRNMF_TRACE("mrnmf_r_svd");
     if (!h) return MRNMF_ERR_INVALID_ARG;
     if (!R || !SVt) return fail(h, MRNMF_ERR_INVALID_ARG, "R and SVt are required");
     if (n < 1 || n > MRNMF_NMAX) return fail(h, MRNMF_ERR_INVALID_ARG, "n must be in [1, 256]");
