@@ -85,5 +85,31 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+def build_sanitized(out_dir: str) -> str:
+    """A copy of the library whose host code is built with AddressSanitizer and
+    UndefinedBehaviorSanitizer (the device code is unchanged), written to
+    out_dir.  Load it in a process that preloads the ASan runtime."""
+    os.makedirs(out_dir, exist_ok=True)
+    nvcc = _nvcc()
+    san = ["-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined", "-Xcompiler",
+           "-fno-omit-frame-pointer"]
+
+    def compile_one(src):
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
+        r = subprocess.run([nvcc, *ARCH, *NVCC_FLAGS, *san, "-c", src, "-o", obj], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+        return obj
+
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(compile_one, _sources()))
+    lib = os.path.join(out_dir, "libmrnmf_sanitized.so")
+    r = subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "static", *san[:4], "-o", lib, *objs, "-lpthread", "-ldl",
+                        "-lrt"], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    return lib
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))
