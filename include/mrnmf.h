@@ -291,14 +291,18 @@ mrnmf_status mrnmf_factorize_host(mrnmf_handle* handle, const float* X, int64_t 
  * (the pass uses fewer row streams when n is large so the scratch fits).
  *   X      device, m-by-n row-major float32      R device n*n doubles out
  *   colsum device n doubles out (nullable)
- *   status device int32 out (nullable): 0, or the first device-side error
- *          (MRNMF_ERR_BAD_INPUT), valid once the stream reaches it.
+ *   status device int32 out (required): 0, or the first device-side error
+ *          (MRNMF_ERR_BAD_INPUT), valid once the stream reaches it.  A NULL
+ *          status is rejected with MRNMF_ERR_INVALID_ARG, because this entry
+ *          has no handle to keep the error in.
  * Returns after enqueuing on `stream`; argument errors return at once.
  * All calls share the one array per device: calls that overlap on the GPU
  * race and give wrong results, so serialise them.  The array keeps the last
  * call's contents; every call clears what must start at zero.  The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress),
- * so make that first call before any stream capture.
+ * so make that first call before any stream capture.  That address is kept
+ * for the life of the process: after cudaDeviceReset on a device, do not call
+ * this entry point again in the same process.
  */
 mrnmf_status mrnmf_tsqr_r_noalloc(const float* X, int64_t m, int32_t n, int64_t ldx, double* R, double* colsum,
                                   int32_t* status, void* stream);

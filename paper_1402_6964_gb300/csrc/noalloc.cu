@@ -21,18 +21,23 @@
 //    that must start at zero before its kernels read them;
 //  - the first call on each device resolves the array's device address with
 //    cudaGetSymbolAddress (the host-side name is only a stand-in for it), so
-//    make that first call before any stream capture.
+//    make that first call before any stream capture; the address is cached
+//    per device for the life of the process, so after a cudaDeviceReset the
+//    entry point must not be called again in that process;
+//  - the caller must pass a status word: device-side errors (a negative or
+//    NaN entry of X) are reported there and nowhere else.
 
 #include <mutex>
 
 #include "../../include/mrnmf.h"
 #include "internal.h"
+#include "leaf.h"
 #include "trace.h"
 
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
-constexpr size_t kStatusBytes = 256;  // leading bytes: the status word when the caller passes none
+constexpr size_t kStatePad = 256;  // the pass state starts 256 bytes into the array
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -64,7 +69,7 @@ extern "C" mrnmf_status mrnmf_tsqr_r_noalloc(const float* X, int64_t m, int32_t 
                                              double* colsum, int32_t* status, void* stream)
 {
     MRNMF_TRACE("mrnmf_tsqr_r_noalloc");
-    if (!X || !R) return MRNMF_ERR_INVALID_ARG;
+    if (!X || !R || !status) return MRNMF_ERR_INVALID_ARG;
     if (n < 1 || n > MRNMF_NMAX || m < n || ldx < n) return MRNMF_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     void* base = nullptr;
@@ -75,14 +80,24 @@ extern "C" mrnmf_status mrnmf_tsqr_r_noalloc(const float* X, int64_t m, int32_t 
     st.k = 0;
     st.fp64 = 0;
     st.tc = 0;
-    st.P = mrnmf::choose_streams(n, 0, 0, 0, m);
-    // fewer row streams when their triangles would not fit the fixed array
-    const size_t avail = kNoAllocScratchBytes - kStatusBytes;
-    while (st.P > 1 && mrnmf::pass_state_bytes(n, 0, st.P, 0) > avail) st.P = st.P * 3 / 4;
-    if (mrnmf::pass_state_bytes(n, 0, st.P, 0) > avail) return MRNMF_ERR_INVALID_ARG;
-    mrnmf::pass_state_carve(st, static_cast<unsigned char*>(base) + kStatusBytes);
+    // The usual stream count, or the largest one whose state fits the array
+    // (the state grows with P), kept a multiple of the warp leaf's streams per
+    // CTA where that leaf serves n so that the pass does not change kernels.
+    const int P0 = mrnmf::choose_streams(n, 0, 0, 0, m);
+    const size_t avail = kNoAllocScratchBytes - kStatePad;
+    int lo = 1, hi = P0;
+    if (mrnmf::pass_state_bytes(n, 0, 1, 0) > avail) return MRNMF_ERR_INVALID_ARG;
+    while (lo < hi) {  // largest P in [1, P0] with pass_state_bytes(P) <= avail
+        const int mid = lo + (hi - lo + 1) / 2;
+        if (mrnmf::pass_state_bytes(n, 0, mid, 0) <= avail) lo = mid;
+        else hi = mid - 1;
+    }
+    st.P = lo;
+    const int w = mrnmf::warp_leaf_warps_per_cta();
+    if (st.P < P0 && mrnmf::warp_leaf_supported(n, 0) && st.P >= w) st.P -= st.P % w;
+    mrnmf::pass_state_carve(st, static_cast<unsigned char*>(base) + kStatePad);
 
-    int* word = status ? reinterpret_cast<int*>(status) : static_cast<int*>(base);
+    int* word = reinterpret_cast<int*>(status);
     if (cudaMemsetAsync(word, 0, sizeof(int), s) != cudaSuccess) return MRNMF_ERR_CUDA;
     if (mrnmf::pass_reset(st, s) != cudaSuccess) return MRNMF_ERR_CUDA;
     if (mrnmf::pass_push(st, X, m, ldx, 0, 1, word, s) != cudaSuccess) return MRNMF_ERR_CUDA;

@@ -136,8 +136,10 @@ def kernel_launches() -> int:
 
 def tsqr_r_noalloc(X, R, colsum=None, status=None, stream=None) -> int:
     """mrnmf_tsqr_r_noalloc: R (and colsum) of a float32 CUDA X into caller
-    buffers, with no device allocation inside the library.  Returns the
-    C status of the call (device-side errors land in `status`)."""
+    buffers, with no device allocation inside the library.  `status` is a
+    one-element int32 CUDA tensor and is required (None is passed as NULL,
+    which the library rejects).  Returns the C status of the call; device-side
+    errors land in `status`."""
     _check_X(X)
     m, n = X.shape
     return int(load().mrnmf_tsqr_r_noalloc(_ptr(X), m, n, X.stride(0), _ptr(R), _ptr(colsum), _ptr(status),
