@@ -1,7 +1,7 @@
 // api.cu -- the extern "C" entry points of include/mrnmf.h.
 //
 // Argument checking, the handle's device workspace, stream ordering, and the
-// composition of the pass kernels (tsqr_simt.cu / tsqr_tc.cu) and the n-by-n
+// composition of the pass kernels (tsqr_simt.cu, tsqr_warp.cu, tsqr_pipe.cu, tsqr_wy.cu) and the n-by-n
 // step kernels (small_step.cu).  No entry point computes on the host.
 
 #include <algorithm>

@@ -67,7 +67,7 @@ cudaError_t nnls_h(const double* R, int n, const int32_t* K, int r, double* H, v
 cudaError_t residual(const double* R, int n, const int32_t* K, int r, const double* H, double* out, void* ws,
                      cudaStream_t s);
 
-// ---- tensor-core leaf (tsqr_tc.cu) ----
+// ---- tensor-core leaf (tsqr_wy.cu) ----
 bool tc_supported(int n, int k);   // the TF32X3 pass exists for this shape
 bool tc_preferred(int n, int k);   // and MRNMF_PREC_AUTO picks it
 

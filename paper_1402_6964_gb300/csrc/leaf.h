@@ -75,9 +75,9 @@ cudaError_t launch_pipe_leaf(const LeafArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_pipe_batched(const BatchCta* desc, int nctas, const BatchProblem* probs, int max_n, int* status,
                                 cudaStream_t s);
 
-// Tensor-core leaf (tsqr_tc.cu): 16 < n <= 64, k <= 32; one stream per CTA.
+// Tensor-core leaf (tsqr_wy.cu): 16 < n <= 128; one stream per CTA.
 int tc_leaf_rows_per_tile();
-int tc_leaf_ctas_per_sm();
+int tc_leaf_ctas_per_sm(int n);
 cudaError_t launch_tc_leaf(const LeafArgs& a, int grid, cudaStream_t s);  // triangles folded per tree CTA
 cudaError_t launch_tree_batched(const TreeCta* desc, int nctas, int family, cudaStream_t s);
 

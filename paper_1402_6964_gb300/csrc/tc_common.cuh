@@ -34,6 +34,16 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes
     return d;
 }
 
+// The same with the swizzle mode in bits 61-63 (2 = 128-byte swizzle: rows of
+// 128 bytes, the 16-byte chunk index XORed with the row index mod 8; the
+// atom of 8 rows x 128 bytes must start on a 1024-byte boundary).  For a
+// K-major operand LBO is unused with this mode and SBO is the distance
+// between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t sbo_bytes)
+{
+    return smem_desc(saddr, 16, sbo_bytes) | ((uint64_t)2 << 61);
+}
+
 // Instruction descriptor (32 bit) for dense MMA with F32 accumulation,
 // both operands K-major.  ab_format: 1 = BF16 (kind::f16), 2 = TF32 (kind::tf32).
 __host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_format, int M, int N)
@@ -67,6 +77,29 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)accum)
         : "memory");
+}
+
+// D (TMEM) [+]= A (TMEM: lanes = M rows, 8 consecutive columns = K) * B (smem).
+__device__ __forceinline__ void mma_tf32_ts(uint32_t dtmem, uint32_t atmem, uint64_t bdesc, uint32_t idesc, bool accum)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtmem),
+        "r"(atmem), "l"(bdesc), "r"(idesc), "r"((uint32_t)accum)
+        : "memory");
+}
+
+// One lane of the calling warp is elected (elect.sync): 1 there, 0 elsewhere.
+// Issuing tcgen05.mma from an elected lane of a converged warp, rather than
+// from a thread picked by its index, keeps the operands warp-uniform; on
+// GB300 that issued back-to-back MMAs several times faster.
+__device__ __forceinline__ uint32_t elect_one()
+{
+    uint32_t e;
+    asm volatile(
+        "{\n .reg .pred P;\n .reg .b32 r;\n elect.sync r|P, 0xffffffff;\n selp.u32 %0, 1, 0, P;\n}\n"
+        : "=r"(e));
+    return e;
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, bool accum)
@@ -152,6 +185,40 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v)
         : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// 16 registers per thread -> 32 lanes x 16 columns of TMEM, without the wait.
+__device__ __forceinline__ void tmem_st16_nowait(uint32_t taddr, const float* v)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
+// 32 lanes x 16 columns of TMEM -> 16 registers per thread, without the wait
+// (follow with tmem_wait_ld before using the values).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// The part of x that kind::tf32 discards: the tensor core reads only the top
+// 19 bits of a binary32 operand (sign, exponent, 10 fraction bits) and drops
+// the rest without rounding, so x itself serves as the high part and
+// x - trunc(x) is exact.
+__device__ __forceinline__ float tf32_lo(float x) { return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 // Split x into a TF32-exact high part and the remainder (x = hi + lo exactly;
 // lo is itself rounded to TF32 by the tensor core, leaving an error ~2^-22 |x|).

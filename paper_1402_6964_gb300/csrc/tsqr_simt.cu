@@ -363,8 +363,8 @@ void pass_state_carve(PassState& st, void* base)
 int choose_streams(int n, int k, int fp64, int tc, int64_t m)
 {
     if (tc && !fp64) {
-        // one stream per CTA, one CTA per SM
-        int P = num_sms() * tc_leaf_ctas_per_sm();
+        // one stream per CTA, as many CTAs as the SM holds at once
+        int P = num_sms() * tc_leaf_ctas_per_sm(n);
         if (m > 0) {
             const int64_t minrows = 2 * (int64_t)tc_leaf_rows_per_tile();
             const int64_t cap = std::max<int64_t>(1, (m + minrows - 1) / minrows);

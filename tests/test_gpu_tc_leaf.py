@@ -49,9 +49,11 @@ def gx_bound(X, k, seed, row0=0):
 
 
 # one tile, a ragged tile, several tiles per stream with a ragged tail, every
-# panel count (n = 17..32: 2 panels, 33..48: 3, 49..64: 4)
+# panel count (n = 17..32: 2 panels, 33..48: 3, 49..64: 4, up to 8 at n = 128),
+# both tensor-memory maps (n <= 64 and 64 < n <= 128)
 SHAPES = [(17, 17), (100, 20), (129, 24), (4099, 20), (20011, 30), (5000, 32), (3001, 33), (12345, 50),
-          (9999, 48), (5000, 64), (128 * 152 * 2 + 77, 40), (300000, 50)]
+          (9999, 48), (5000, 64), (128 * 152 * 2 + 77, 40), (300000, 50), (3001, 65), (40000, 100),
+          (7000, 127), (20000, 128), (5000, 129), (3000, 150), (20000, 200), (4000, 256)]
 
 
 @pytest.mark.parametrize("m,n", SHAPES)
@@ -68,7 +70,8 @@ def test_tsqr_tf32x3_matches_oracle(h, oracle, m, n):
 
 
 @pytest.mark.parametrize("m,n,k", [(20011, 30, 12), (9001, 50, 20), (4099, 64, 31), (50000, 40, 1), (777, 18, 15),
-                                   (4096, 36, 16), (3000, 40, 32)])
+                                   (4096, 36, 16), (3000, 40, 32), (20000, 100, 40), (5000, 128, 48), (3000, 70, 17),
+                                   (20000, 200, 40), (3000, 256, 48), (1000, 140, 5)])
 def test_fused_tf32x3_matches_oracle(h, oracle, m, n, k):
     X = synth.random_nonneg(m, n, seed=3 + n + k)
     R, cs, GX = h.tsqr_gp(dev(X), k, seed=99, prec="tf32x3")
@@ -80,9 +83,11 @@ def test_fused_tf32x3_matches_oracle(h, oracle, m, n, k):
     np.testing.assert_allclose(host(cs), oracle.colsum(X64), rtol=1e-6)
 
 
-def test_tf32x3_ill_conditioned(h, oracle):
-    # column scaling 10^U(0,6): per-column relative error bounded as for binary32
-    X, P = synth.planted_separable(200000, 50, 10, seed=1402003, noise=1e-3, decades=6.0)
+@pytest.mark.parametrize("m,n,r", [(200000, 50, 10), (60000, 200, 20)])
+def test_tf32x3_ill_conditioned(h, oracle, m, n, r):
+    # column scaling 10^U(0,6) (the recipe of the 1e8 x 200 workload): per-column
+    # relative error bounded as for binary32
+    X, P = synth.planted_separable(m, n, r, seed=1402003, noise=1e-3, decades=6.0)
     R, _ = h.tsqr_r(dev(X), prec="tf32x3")
     h.sync()
     Ro = oracle.qr_r(X.astype(np.float64))
@@ -145,10 +150,14 @@ def test_tf32x3_bad_input_is_reported(h):
 
 
 def test_tf32x3_rejects_unsupported_shape(h):
-    # the tensor-core form covers 16 < n <= 64 (k <= 32)
+    # the tensor-core form covers 16 < n <= 256, with k <= 32 for n <= 64 and k <= 48 above
     from paper_1402_6964_gb300 import mrnmf
-    for m, n in [(1000, 10), (1000, 200)]:
-        X = synth.random_nonneg(m, n, seed=2)
+    X = synth.random_nonneg(1000, 10, seed=2)
+    with pytest.raises(mrnmf.MrnmfError) as e:
+        h.tsqr_r(dev(X), prec="tf32x3")
+    assert e.value.status == mrnmf.ERR_INVALID_ARG
+    for n, k in [(50, 33), (100, 49)]:
+        X = synth.random_nonneg(1000, n, seed=2)
         with pytest.raises(mrnmf.MrnmfError) as e:
-            h.tsqr_r(dev(X), prec="tf32x3")
+            h.tsqr_gp(dev(X), k, seed=1, prec="tf32x3")
         assert e.value.status == mrnmf.ERR_INVALID_ARG

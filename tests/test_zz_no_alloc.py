@@ -19,6 +19,8 @@ with different shapes (so stale contents of the shared array would show):
 This file is collected last so that a run stopping at its first failure has
 already run every other test; it passes alone in a fresh process too.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -93,11 +95,14 @@ def test_noalloc_allocates_nothing(lib):
         assert mrnmf.tsqr_r_noalloc(Xd, R, cs, status) == mrnmf.OK
         torch.cuda.synchronize()
         R0 = R.clone()
+        gc.collect()
+        torch.cuda.synchronize()
         used0, free0 = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
         assert mrnmf.tsqr_r_noalloc(Xd, R, cs, status) == mrnmf.OK
         torch.cuda.synchronize()
-        assert torch.cuda.memory_allocated() == used0
-        assert torch.cuda.mem_get_info()[0] == free0
+        # neither torch's allocator nor the driver gave out memory during the call
+        assert torch.cuda.memory_allocated() <= used0
+        assert torch.cuda.mem_get_info()[0] >= free0
         assert int(status.item()) == 0
         assert torch.equal(R, R0)  # same input, same result: no state leaks between calls
 
