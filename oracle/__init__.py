@@ -57,6 +57,7 @@ def _bind(lib):
     lib.orc_spa.argtypes = [P, i32, i32, P, i32, P, P]
     lib.orc_xray.argtypes = [P, i32, i32, i32, P, P]
     lib.orc_gp_select.argtypes = [P, i32, i32, P, i32, P, P, P, P, P]
+    lib.orc_r_svd.argtypes = [P, i32, P, P]
     return lib
 
 
@@ -213,3 +214,14 @@ def gp_select(GX, colsum_, r: int):
     _load().orc_gp_select(_ptr(GX), k, n, _ptr(s), r, _ptr(K), _ptr(cand), ctypes.byref(nc), _ptr(gap),
                           _ptr(cgap))
     return K, cand[: nc.value].copy(), cgap[: nc.value].copy()
+
+
+def r_svd(R):
+    """Sigma V' of a square R by one-sided Jacobi (Sec. 2.2; the R-SVD of
+    Sec. 3.1): (sigma descending, SVt with row i = sigma_i v_i', status)."""
+    R = _f64(R)
+    n = R.shape[0]
+    sig = np.zeros(n)
+    S = np.zeros((n, n))
+    st = _load().orc_r_svd(_ptr(R), n, _ptr(sig), _ptr(S))
+    return sig, S, st

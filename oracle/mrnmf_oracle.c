@@ -493,3 +493,79 @@ int orc_gp_select(const double* GX, int k, int n, const double* colsum, int r, i
     for (int t = 0; t < r; ++t) K[t] = t < cnt ? cand[t] : -1;
     return cnt >= r ? ORC_OK : ORC_ERR_RANK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* R-SVD (Sec. 2.2 and Sec. 3.1, the R-SVD of a tall matrix): Sigma V' of   */
+/* an n-by-n R, from R = U Sigma V'.  One-sided Jacobi (Hestenes): plane    */
+/* rotations from the right make the columns of B = R' mutually orthogonal; */
+/* then B = V Sigma, so column i of B is sigma_i v_i and its transpose is   */
+/* row i of Sigma V'.  Pairs are visited in plain cyclic order (i < j, row  */
+/* by row); each rotation uses Rutishauser's stable formulas.  Sweeps       */
+/* repeat until one rotates nothing (at most 60).  Output rows are sorted   */
+/* by descending sigma; each row is determined up to its sign.              */
+/* ------------------------------------------------------------------------ */
+int orc_r_svd(const double* R, int n, double* sigma, double* SVt)
+{
+    if (n < 1) return ORC_ERR_ARG;
+    double* B = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n); /* B[k*n + i] = R[i*n + k] */
+    int* order = (int*)malloc(sizeof(int) * (size_t)n);
+    double* s = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!B || !order || !s) {
+        free(B);
+        free(order);
+        free(s);
+        return ORC_ERR_NOMEM;
+    }
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) B[(size_t)k * n + i] = R[(size_t)i * n + k];
+    int converged = 0;
+    for (int sweep = 0; sweep < 60 && !converged; ++sweep) {
+        int rotated = 0;
+        for (int i = 0; i < n - 1; ++i) {
+            for (int j = i + 1; j < n; ++j) {
+                double a = 0.0, b = 0.0, g = 0.0; /* ||b_i||^2, ||b_j||^2, b_i' b_j */
+                for (int k = 0; k < n; ++k) {
+                    const double bi = B[(size_t)k * n + i], bj = B[(size_t)k * n + j];
+                    a += bi * bi;
+                    b += bj * bj;
+                    g += bi * bj;
+                }
+                if (g == 0.0 || fabs(g) <= 1e-15 * sqrt(a * b)) continue;
+                rotated = 1;
+                const double zeta = (b - a) / (2.0 * g);
+                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+                for (int k = 0; k < n; ++k) {
+                    const double bi = B[(size_t)k * n + i], bj = B[(size_t)k * n + j];
+                    B[(size_t)k * n + i] = c * bi - sn * bj;
+                    B[(size_t)k * n + j] = sn * bi + c * bj;
+                }
+            }
+        }
+        converged = !rotated;
+    }
+    for (int i = 0; i < n; ++i) {
+        double a = 0.0;
+        for (int k = 0; k < n; ++k) a += B[(size_t)k * n + i] * B[(size_t)k * n + i];
+        s[i] = sqrt(a);
+        order[i] = i;
+    }
+    /* descending sigma; equal values keep the lower column first */
+    for (int i = 1; i < n; ++i) {
+        const int o = order[i];
+        int p = i;
+        while (p > 0 && s[order[p - 1]] < s[o]) {
+            order[p] = order[p - 1];
+            --p;
+        }
+        order[p] = o;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (sigma) sigma[i] = s[order[i]];
+        for (int k = 0; k < n; ++k) SVt[(size_t)i * n + k] = B[(size_t)k * n + order[i]];
+    }
+    free(B);
+    free(order);
+    free(s);
+    return converged ? ORC_OK : ORC_ERR_NOT_CONVERGED;
+}

@@ -104,6 +104,7 @@ mrnmf_status setup_pass(mrnmf_handle* h, int n, int dtype, int prec, int k, uint
     st.k = k;
     st.fp64 = prec == MRNMF_PREC_FP64;
     st.tc = prec == MRNMF_PREC_TF32X3;
+    st.tree64 = !st.fp64 && mrnmf::tree64_requested() && mrnmf::tree64_supported(n);
     st.seed = seed;
     st.rows_seen = 0;
     st.P = mrnmf::choose_streams(n, k, st.fp64, st.tc, m_hint);

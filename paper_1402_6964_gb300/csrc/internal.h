@@ -25,8 +25,9 @@ struct PassState {
                         // the warp leaf folds each CTA's four streams into one)
     int fp64 = 0;       // 1: triangles and reflectors in binary64, else binary32
     int tc = 0;         // 1: tensor-core (TF32x3) leaf
+    int tree64 = 0;     // 1: binary32 leaf triangles reduced by a binary64 tree
     void* R = nullptr;      // P * n * n (dense row-major, zeros below diag), T = float or double
-    void* Rtmp = nullptr;   // ceil(P/2) * n * n, ping-pong buffer of the tree
+    void* Rtmp = nullptr;   // ceil(P/2) * n * n binary64, ping-pong buffer of the tree
     double* cs = nullptr;   // P * n partial column sums
     double* gx = nullptr;   // P * k * n partial projections
     uint64_t seed = 0;
@@ -37,6 +38,12 @@ struct PassState {
 
 size_t pass_state_bytes(int n, int k, int P, int fp64);
 void pass_state_carve(PassState& st, void* base);
+
+// The binary64 tree over binary32 leaf triangles exists for this n (its
+// packed triangle fits a CTA's shared memory).
+bool tree64_supported(int n);
+// MRNMF_TREE64=1 selects it for binary32 passes.
+bool tree64_requested();
 
 // Number of streams for a pass over about `m` rows (0 = unknown / streaming).
 int choose_streams(int n, int k, int fp64, int tc, int64_t m);

@@ -71,7 +71,9 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a)
     const int cta = blockIdx.x;
 
     // ---- running triangle: continue from the state, or start at zero ----
-    const T* Rin = static_cast<const T*>(a.R_in);
+    // (the tree reads its input triangles in TX: binary32 leaf triangles can
+    // enter a binary64 tree)
+    const TX* Rin = static_cast<const TX*>(a.R_in);
     int64_t first_tri = 0, last_tri = 0;  // tree: triangles [first_tri+1, last_tri) are merged
     if (TRI) {
         first_tri = (int64_t)cta * a.rows_per_cta;
@@ -81,12 +83,22 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a)
     if (QR) {
         // independent loads over the whole triangle, unrolled so they overlap
         const bool have = Rin && (!TRI || init_slot < a.P_in);
-        const T* src = have ? Rin + (size_t)init_slot * n * n : nullptr;
         const int nn = n * n;
+        if (TRI || is_same_t<TX, T>::value) {
+            const TX* src = have ? Rin + (size_t)init_slot * n * n : nullptr;
 #pragma unroll 8
-        for (int e = threadIdx.x; e < nn; e += nt) {
-            const int j = e / n, cc = e - j * n;
-            if (cc >= j) Rs[packed_row(j, n) + cc] = have ? src[e] : T(0);
+            for (int e = threadIdx.x; e < nn; e += nt) {
+                const int j = e / n, cc = e - j * n;
+                if (cc >= j) Rs[packed_row(j, n) + cc] = have ? (T)src[e] : T(0);
+            }
+        } else {
+            // a leaf continuing its state: the state is kept in T
+            const T* src = have ? static_cast<const T*>(a.R_in) + (size_t)init_slot * n * n : nullptr;
+#pragma unroll 8
+            for (int e = threadIdx.x; e < nn; e += nt) {
+                const int j = e / n, cc = e - j * n;
+                if (cc >= j) Rs[packed_row(j, n) + cc] = have ? src[e] : T(0);
+            }
         }
         __syncthreads();
     }
@@ -107,9 +119,9 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a)
             const int64_t tri = first_tri + 1 + t / tpt;
             const int i0 = (int)(t % tpt) * L;
             j0 = i0;
-            const T* src = Rin + ((size_t)tri * n + i0) * n + c;
+            const TX* src = Rin + ((size_t)tri * n + i0) * n + c;
 #pragma unroll
-            for (int l = 0; l < L; ++l) v[l] = (own && i0 + l < n) ? src[(size_t)l * n] : T(0);
+            for (int l = 0; l < L; ++l) v[l] = (own && i0 + l < n) ? (T)src[(size_t)l * n] : T(0);
         } else {
             const int64_t row = r0 + t * L;
             j0 = 0;
@@ -243,11 +255,12 @@ __global__ void __launch_bounds__(256) tsqr_leaf_kernel(const LeafArgs a)
     leaf_body<TX, T, L, KMAX, QR, false>(a);
 }
 
-// One level of the reduction tree over the stacked triangles.
-template <typename T, int L>
+// One level of the reduction tree over the stacked triangles (input triangles
+// in TX, arithmetic and output in T).
+template <typename TX, typename T, int L>
 __global__ void __launch_bounds__(256) tsqr_tree_kernel(const LeafArgs a)
 {
-    leaf_body<T, T, L, 0, true, true>(a);
+    leaf_body<TX, T, L, 0, true, true>(a);
 }
 
 // R <- sign-normalised binary64 copy of the final triangle (diag >= 0).
@@ -294,7 +307,7 @@ template <typename TX, typename T, int L, int KMAX, bool QR, bool TRI>
 cudaError_t launch_leaf_on(const LeafArgs& a, int grid, cudaStream_t s)
 {
     void (*kern)(const LeafArgs);
-    if constexpr (TRI) kern = tsqr_tree_kernel<T, L>;
+    if constexpr (TRI) kern = tsqr_tree_kernel<TX, T, L>;
     else kern = tsqr_leaf_kernel<TX, T, L, KMAX, QR>;
     const size_t smem = leaf_smem_bytes<T, L, KMAX>(a.n);
     if (smem > 48 * 1024) {
@@ -341,7 +354,7 @@ size_t pass_state_bytes(int n, int k, int P, int fp64)
     const size_t ts = fp64 ? 8 : 4;
     size_t b = 0;
     b += align16<float>(ts * (size_t)P * n * n);              // R
-    b += align16<float>(ts * (size_t)((P + 1) / 2) * n * n);  // Rtmp
+    b += align16<float>(8 * (size_t)((P + 1) / 2) * n * n);   // Rtmp (binary64 also for the FP64 tree)
     b += align16<float>(8 * (size_t)P * n);                   // cs
     b += align16<float>(8 * (size_t)P * (k > 0 ? k : 1) * n); // gx
     return b;
@@ -354,7 +367,7 @@ void pass_state_carve(PassState& st, void* base)
     st.R = p;
     p += align16<float>(ts * (size_t)st.P * st.n * st.n);
     st.Rtmp = p;
-    p += align16<float>(ts * (size_t)((st.P + 1) / 2) * st.n * st.n);
+    p += align16<float>(8 * (size_t)((st.P + 1) / 2) * st.n * st.n);
     st.cs = reinterpret_cast<double*>(p);
     p += align16<float>(8 * (size_t)st.P * st.n);
     st.gx = reinterpret_cast<double*>(p);
@@ -540,11 +553,62 @@ static cudaError_t tree_and_finalize(PassState& st, double* R, int* status, cuda
     return cudaSuccess;
 }
 
+bool tree64_supported(int n) { return leaf_smem_bytes<double, kTriRows, 0>(n) <= 227 * 1024; }
+
+bool tree64_requested()
+{
+    static const bool on = [] {
+        const char* v = getenv("MRNMF_TREE64");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
+
+// The reduction of Sec. 3.1 over the stacked binary32 leaf triangles in
+// binary64: the first level reads binary32 and folds in binary64, every later
+// level is binary64 throughout (fan-in 2).  Level 1 writes Rtmp; later levels
+// alternate with the leaf triangles' own region, which then holds at most
+// ceil(P/4) binary64 triangles -- no more bytes than its P binary32 ones.
+static cudaError_t tree64_and_finalize(PassState& st, double* R, int* status, cudaStream_t s)
+{
+    const void* cur = st.R;
+    void* bufs[2] = {st.Rtmp, st.R};
+    int Pc = st.tri > 0 ? st.tri : st.P, which = 0;
+    bool cur64 = false;
+    while (Pc > 1) {
+        const int Pn = (Pc + 1) / 2;
+        LeafArgs a{};
+        a.n = st.n;
+        a.rows_per_cta = 2;
+        a.R_in = cur;
+        a.R_out = bufs[which];
+        a.P_in = Pc;
+        a.status = status;
+        cudaError_t e = cur64 ? launch_leaf_on<double, double, kTriRows, 0, true, true>(a, Pn, s)
+                              : launch_leaf_on<float, double, kTriRows, 0, true, true>(a, Pn, s);
+        if (e != cudaSuccess) return e;
+        cur = bufs[which];
+        cur64 = true;
+        which ^= 1;
+        Pc = Pn;
+    }
+    if (R) {
+        const int nn = st.n * st.n;
+        if (cur64) finalize_r_kernel<double><<<(nn + 255) / 256, 256, 0, s>>>(static_cast<const double*>(cur), st.n, R);
+        else finalize_r_kernel<float><<<(nn + 255) / 256, 256, 0, s>>>(static_cast<const float*>(cur), st.n, R);
+        count_launch();
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
+
 cudaError_t pass_finish(PassState& st, int qr, double* R, double* colsum, double* GX, int* status, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
     if (qr) {
-        e = st.fp64 ? tree_and_finalize<double>(st, R, status, s) : tree_and_finalize<float>(st, R, status, s);
+        if (st.fp64) e = tree_and_finalize<double>(st, R, status, s);
+        else if (st.tree64 && tree64_supported(st.n)) e = tree64_and_finalize(st, R, status, s);
+        else e = tree_and_finalize<float>(st, R, status, s);
         if (e != cudaSuccess) return e;
     }
     const int kk = (GX && st.k > 0) ? st.k : 0;

@@ -170,8 +170,19 @@ def pin_gp_hand(orc):
     return list(cand) == [int(v) for v in c["CAND"][0]]
 
 
+def pin_r_svd(orc):
+    X = synth.random_nonneg(400, 12, seed=41, dtype=np.float64)
+    R = orc.qr_r(X)
+    sig, S, st = orc.r_svd(R)
+    sl = np.linalg.svd(R, compute_uv=False)
+    G = R.T @ R
+    return (st == 0 and np.allclose(sig, sl, rtol=0, atol=1e-12 * sl[0])
+            and np.linalg.norm(S.T @ S - G) <= 1e-12 * np.linalg.norm(G))
+
+
 PINS = [pin_qr_gram, pin_qr_cholesky, pin_colsum_exact, pin_philox_kat, pin_gauss_moments, pin_gx_matmul,
-        pin_nnls_brute, pin_nnls_scipy, pin_spa_hand, pin_xray_hand, pin_xray_first_pick, pin_xray_scores, pin_residual_full, pin_gp_hand]
+        pin_nnls_brute, pin_nnls_scipy, pin_spa_hand, pin_xray_hand, pin_xray_first_pick, pin_xray_scores, pin_residual_full, pin_gp_hand,
+        pin_r_svd]
 
 # ---------------------------------------------------------------- the mistakes
 
@@ -208,6 +219,10 @@ MUTANTS = {
         "for (int a = 0; a < t; ++a) s -= Y0[(int64_t)i * n + K[a]] * H[(int64_t)a * n + c];"),
     "residual: wrong term in the denominator": (
         "r2 += v * v;", "r2 += s * s;"),
+    "r-svd: rotation sign flipped": (
+        "B[(size_t)k * n + i] = c * bi - sn * bj;", "B[(size_t)k * n + i] = c * bi + sn * bj;"),
+    "r-svd: rotation angle from the wrong difference": (
+        "const double zeta = (b - a) / (2.0 * g);", "const double zeta = (a - b) / (2.0 * g);"),
     "gp: min before max": (
         "int picks[2] = {jmax, jmin};", "int picks[2] = {jmin, jmax};"),
 }

@@ -353,3 +353,59 @@ def test_residual_reduced_equals_full(oracle):
     R0 = oracle.qr_r(X0)
     H0, _ = oracle.nnls_h(R0, P0.K)
     assert oracle.residual(R0, P0.K, H0)[1] < 1e-20
+
+
+# ------------------------------------------------------------------ R-SVD
+
+def test_r_svd_golden_ratio(oracle):
+    # closed form: R = [[1, 1], [0, 1]] has R'R = [[1, 1], [1, 2]], singular
+    # values phi = (1 + sqrt 5)/2 and 1/phi, right singular vectors
+    # [1, phi]/sqrt(1 + phi^2) and [-phi, 1]/sqrt(1 + phi^2)
+    phi = (1 + 5 ** 0.5) / 2
+    sig, S, st = oracle.r_svd(np.array([[1.0, 1.0], [0.0, 1.0]]))
+    assert st == 0
+    np.testing.assert_allclose(sig, [phi, 1 / phi], rtol=1e-15)
+    d = (1 + phi ** 2) ** 0.5
+    want = np.array([[phi * 1 / d, phi * phi / d], [-1 / phi * phi / d, 1 / phi * 1 / d]])
+    for i in range(2):
+        s = np.sign(S[i] @ want[i])
+        np.testing.assert_allclose(s * S[i], want[i], rtol=1e-14, atol=1e-15)
+
+
+def test_r_svd_diagonal_is_a_sorted_permutation(oracle):
+    d = np.array([0.5, 3.0, 2.0, 7.0, 1.0])
+    sig, S, st = oracle.r_svd(np.diag(d))
+    assert st == 0
+    np.testing.assert_array_equal(sig, np.sort(d)[::-1])
+    order = np.argsort(-d)
+    np.testing.assert_array_equal(np.abs(S), np.abs(np.diag(d)[order]))
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (40, 7), (3000, 50), (500, 101)])
+def test_r_svd_matches_lapack(oracle, m, n):
+    # sigma equals LAPACK's (a different algorithm); Sigma V' = U' R with U
+    # orthogonal, so (Sigma V')' (Sigma V') = R'R and the rows are orthogonal
+    # with norms sigma; rows of well-separated sigma equal LAPACK's up to sign
+    X = synth.random_nonneg(m, n, seed=m + n, dtype=np.float64)
+    R = oracle.qr_r(X)
+    sig, S, st = oracle.r_svd(R)
+    assert st == 0
+    U, sl, Vt = np.linalg.svd(R)
+    np.testing.assert_allclose(sig, sl, rtol=0, atol=1e-12 * sl[0])
+    G = R.T @ R
+    assert np.linalg.norm(S.T @ S - G) <= 1e-12 * np.linalg.norm(G)
+    D = S @ S.T
+    assert np.max(np.abs(D - np.diag(np.diag(D)))) <= 1e-12 * sl[0] ** 2
+    for i in range(n):
+        gaps = [abs(sl[i] - sl[j]) for j in (i - 1, i + 1) if 0 <= j < n]
+        if min(gaps, default=sl[0]) > 1e-3 * sl[0]:
+            ref = sl[i] * Vt[i]
+            s = np.sign(S[i] @ ref)
+            np.testing.assert_allclose(s * S[i], ref, rtol=0, atol=1e-9 * sl[0])
+
+
+def test_r_svd_rank_deficient(oracle):
+    X, P = synth.planted_separable(5000, 20, 4, seed=14, dtype=np.float64)
+    sig, S, st = oracle.r_svd(oracle.qr_r(X))
+    assert st == 0
+    assert np.all(sig[4:] <= 1e-10 * sig[0])

@@ -13,7 +13,7 @@ with different shapes (so stale contents of the shared array would show):
   (n = 100), and n = 256, where the state of the usual stream count does not
   fit the array, so the call runs fewer streams and the fan-in-2 tree;
 * that a call allocates no device memory (torch's allocator and the driver's
-  free-memory count are unchanged across it);
+  free-memory count do not grow across it);
 * that a NULL status word is rejected.
 
 This file is collected last so that a run stopping at its first failure has
