@@ -31,6 +31,9 @@ mrnmf_status fail(mrnmf_handle* h, mrnmf_status s, const std::string& msg)
 
 mrnmf_status cuda_fail(mrnmf_handle* h, cudaError_t e, const char* where)
 {
+    // consume the runtime's record of a non-sticky error, so that it is not
+    // reported again by the next cudaGetLastError of a later, unrelated call
+    (void)cudaGetLastError();
     return fail(h, e == cudaErrorMemoryAllocation ? MRNMF_ERR_NO_MEMORY : MRNMF_ERR_CUDA,
                 std::string(where) + ": " + cudaGetErrorString(e));
 }

@@ -346,7 +346,9 @@ extern "C" mrnmf_status mrnmf_tsqr_r_batched(mrnmf_handle* h, const mrnmf_proble
     const mrnmf::PlanPtrs ptrs = mrnmf::pack_plan(plan, static_cast<unsigned char*>(h->bstage), devb);
     if ((e = cudaMemcpyAsync(devb, h->bstage, desc_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(h, e, "descriptor upload");
-    if ((e = cudaEventRecord(h->ev_bstage, s)) != cudaSuccess) return cuda_fail(h, e, "event");
+    // (not inside a stream capture: a captured record would leave the event
+    // in the graph, and the next eager call could not wait on it)
+    if (!capturing && (e = cudaEventRecord(h->ev_bstage, s)) != cudaSuccess) return cuda_fail(h, e, "event");
     if (cs_bytes && (e = cudaMemsetAsync(devb + cs_off, 0, cs_bytes, s)) != cudaSuccess)
         return cuda_fail(h, e, "partial sums");
     if ((e = mrnmf::run_batched_plan(plan, ptrs, max_n, h->d_status, s)) != cudaSuccess)

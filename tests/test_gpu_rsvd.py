@@ -56,11 +56,12 @@ def test_r_svd_invariants(h, oracle, m, n):
 @pytest.mark.parametrize("m,n", [(100, 7), (5000, 50), (3000, 101), (8000, 200), (2000, 256)])
 def test_r_svd_matches_oracle(h, oracle, m, n):
     """Element by element against the oracle's one-sided Jacobi (binary64,
-    its own cyclic pair order): sigma within 1e-12 sigma_max, and every row
-    of Sigma V' whose sigma is separated from its neighbours by more than
-    1e-3 sigma_max within 1e-9 sigma_max after aligning the row's sign (a
-    row of a near-multiple singular value is determined only up to a rotation
-    in its subspace; those rows are covered by the invariants above)."""
+    its own cyclic pair order): sigma within 1e-12 sigma_max, and every row of
+    Sigma V' after aligning its sign, within 1e-12 sigma_max^2 / gap_i where
+    gap_i is the distance from sigma_i to its nearest neighbour (first-order
+    perturbation of a singular vector: error / sigma_max ~ eps sigma_max /
+    gap).  Rows whose gap is below 1e-6 sigma_max, whose bound would say
+    nothing, are left to the invariants above."""
     X = synth.random_nonneg(m, n, seed=13 * n + 1)
     Ro = oracle.qr_r(X.astype(np.float64))
     sig, SVt = h.r_svd(dev(Ro))
@@ -71,12 +72,12 @@ def test_r_svd_matches_oracle(h, oracle, m, n):
     np.testing.assert_allclose(s, so, rtol=0, atol=1e-12 * so[0])
     checked = 0
     for i in range(n):
-        gaps = [abs(so[i] - so[j]) for j in (i - 1, i + 1) if 0 <= j < n]
-        if min(gaps, default=so[0]) > 1e-3 * so[0]:
+        gap = min([abs(so[i] - so[j]) for j in (i - 1, i + 1) if 0 <= j < n], default=so[0])
+        if gap > 1e-6 * so[0]:
             sgn = 1.0 if S[i] @ So[i] >= 0 else -1.0
-            np.testing.assert_allclose(sgn * S[i], So[i], rtol=0, atol=1e-9 * so[0])
+            np.testing.assert_allclose(sgn * S[i], So[i], rtol=0, atol=1e-12 * so[0] ** 2 / gap)
             checked += 1
-    assert checked >= min(n, 3)
+    assert checked >= n // 2
 
 
 def test_r_svd_rank_deficient(h, oracle):
