@@ -131,26 +131,40 @@ def cpu_oracle_step(X: np.ndarray, w, rows: int):
 
 
 def run_reference(args):
+    """The oracle as it stands on every host core: one spawned process per core,
+    each step running the whole path on its own `ref_rows`-row chunk of the
+    workload (a bounded sample); GB/s = rows of all processes / wall time."""
+    import multiprocessing as mp
+
     from paper_1402_6964_gb300 import synth
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     w = synth.WORKLOADS[args.workload]
     rows = args.ref_rows
-    X, _ = synth.workload_matrix(w, m=rows)
-    for _ in range(args.warmup):
-        cpu_oracle_step(X, w, rows)
-    ts = [cpu_oracle_step(X, w, rows) for _ in range(args.steps)]
+    cores, model = host_cpu_info()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        jobs = [(args.workload, c, rows) for c in range(cores)]
+        for _ in range(args.warmup):
+            pool.map(_oracle_chunk_worker, jobs)
+        ts = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_chunk_worker, jobs)
+            ts.append(time.perf_counter() - t0)
     t = sum(ts)
-    gbs = 4.0 * rows * w.n * args.steps / t / 1e9
+    gbs = 4.0 * rows * w.n * cores * args.steps / t / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": w.name, "m": w.m, "n": w.n, "r": w.r, "k": w.k, "prec": args.prec,
                        "parallelism": "replicas" if args.gpus > 1 else "single GPU"},
-            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{rows} rows per step, drawn by the {w.m}-row workload's generator"},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle", "nproc": cores,
+                             "cpu_model": model,
+                             "sample": f"{cores} processes per step, each the whole path (pass + SPA/XRAY/GP + "
+                                       f"NNLS + residual) on its own {rows}-row chunk of the {w.m}-row workload"},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -189,7 +203,7 @@ def run_gp_pass(args):
     h.close()
 
 
-def run_batched(args):
+def run_batched(args, quiet=False):
     """256 independent problems (m log-uniform in [1e4, 1e7], n uniform in
     10..128, r uniform in 3..min(16, n/2), sigma = 1e-3), drawn on the device:
     rows/s of per-matrix mrnmf_tsqr_r calls, of one mrnmf_tsqr_r_batched call,
@@ -255,11 +269,15 @@ def run_batched(args):
     for k, ms in res.items():
         line[k] = {"ms": ms, "rows_per_s": rows / ms * 1e3, "GBps": nbytes / ms / 1e6}
     line["value"] = line["batched_graph"]["rows_per_s"]
-    print(json.dumps(line), flush=True)
     h.close()
+    del Xs, outs
+    torch.cuda.empty_cache()
+    if not quiet:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_stream(args):
+def run_stream(args, quiet=False):
     """Flow-cytometry-shaped stream (1.6e9 x 25, r = 8, log-normal W,
     Dirichlet(0.5), sigma = 1e-2), or with --workload kron_fc_1p6e9x25 the
     Kronecker-structured A kron A (A: 40,000 x 5, r_A = 4, so r = 16): 64M-row
@@ -316,14 +334,138 @@ def run_stream(args):
     nbytes = 4.0 * m * w.n
     hbm, _, src = _peaks()
     gbs = nbytes / (push_ms + end_ms) / 1e6
-    print(json.dumps({"mode": "stream", "metric": "streamed TSQR pass GB/s of X (chunk reads)", "value": gbs,
-                      "unit": "GB/s", "ms_pass": push_ms + end_ms, "ms_generation": gen_ms, "chunks": nchunks,
-                      "chunk_rows": chunk, "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm,
-                                                        "unit": "GB/s", "frac": gbs / hbm, "peak_source": src},
-                      "K_spa": sorted(K.cpu().numpy().tolist()), "K_planted": Kp.tolist(),
-                      "residual_rel": float(out[1].item()),
-                      "config": {"workload": w.name, "m": m, "n": w.n, "r": w.r, "k": w.k}}), flush=True)
+    line = {"mode": "stream", "metric": "streamed TSQR pass GB/s of X (chunk reads)", "value": gbs,
+            "unit": "GB/s", "ms_pass": push_ms + end_ms, "ms_generation": gen_ms, "chunks": nchunks,
+            "chunk_rows": chunk, "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm,
+                                              "unit": "GB/s", "frac": gbs / hbm, "peak_source": src},
+            "K_spa": sorted(K.cpu().numpy().tolist()), "K_planted": Kp.tolist(),
+            "residual_rel": float(out[1].item()),
+            "config": {"workload": w.name, "m": m, "n": w.n, "r": w.r, "k": w.k}}
     h.close()
+    del buf
+    torch.cuda.empty_cache()
+    if not quiet:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def tc_form_available(n: int, k: int) -> bool:
+    """The tensor-core (TF32x3) pass exists for this shape (the library's rule)."""
+    return 16 < n <= 256 and k <= (32 if n <= 64 else 48)
+
+
+def run_illcond_forms(args, quiet=False):
+    """The 1e8 x 200 ill-conditioned workload (80 GB, drawn on the device):
+    the fused pass (R, column sums, GX with k = 40) in each arithmetic form,
+    with each form's R error by the Gram identity (binary64 X'X accumulated on
+    the device)."""
+    import torch
+
+    from paper_1402_6964_gb300 import build, mrnmf, synth
+
+    build.build()
+    w = synth.WORKLOADS["illcond_1e8x200"]
+    m = args.rows or w.m
+    P = synth.planted_structure(w.n, w.r, w.seed, w.alpha, w.decades)
+    Xd = torch.empty((m, w.n), dtype=torch.float32, device="cuda")
+    ch = 1 << 23
+    for c0 in range(0, m, ch):
+        rows = min(ch, m - c0)
+        synth.device_planted(rows, w.n, w.r, w.seed, noise=w.noise, alpha=w.alpha, w_dist=w.w_dist,
+                             chunk=c0 // ch, P=P, out=Xd[c0:c0 + rows])
+    torch.cuda.synchronize()
+    Gd = torch.zeros((w.n, w.n), dtype=torch.float64, device="cuda")
+    for c0 in range(0, m, 1 << 21):
+        Xc = Xd[c0:c0 + (1 << 21)].double()
+        Gd += Xc.T @ Xc
+        del Xc
+    Gram = Gd.cpu().numpy()
+    del Gd
+    h = mrnmf.Handle()
+    n, k = w.n, w.k
+    R = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    cs = torch.empty(n, dtype=torch.float64, device="cuda")
+    GX = torch.empty((k, n), dtype=torch.float64, device="cuda")
+    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0.record()
+    l1.record()
+    forms = {}
+    nbytes = 4.0 * m * n
+    for form in ("fp32", "tf32x3"):
+        if form == "tf32x3" and not tc_form_available(n, k):
+            continue
+        h.tsqr_gp(Xd, k, w.seed, prec=form, out=(R, cs, GX))  # warm-up
+        h.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        h.profile_events(l0, l1)
+        leaf = 0.0
+        a.record()
+        for _ in range(reps):
+            h.tsqr_gp(Xd, k, w.seed, prec=form, out=(R, cs, GX))
+        b.record()
+        torch.cuda.synchronize()
+        leaf = l0.elapsed_time(l1)
+        h.profile_events(None, None)
+        h.sync()
+        ms = a.elapsed_time(b) / reps
+        Rh = R.cpu().numpy()
+        forms[form] = {"pass_ms": ms, "GBps": nbytes / ms / 1e6, "leaf_ms": leaf,
+                       "r_error_gram_identity": float(np.linalg.norm(Rh.T @ Rh - Gram) / np.linalg.norm(Gram))}
+    h.close()
+    del Xd, R, cs, GX
+    torch.cuda.empty_cache()
+    line = {"mode": "illcond", "workload": w.name, "m": m, "n": n, "k": k, "forms": forms}
+    if "tf32x3" in forms:
+        line["mixed_over_fp32"] = forms["fp32"]["pass_ms"] / forms["tf32x3"]["pass_ms"]
+    if not quiet:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def host_cpu_info():
+    """Core count and model of the host the oracle runs on (nproc, lscpu)."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return cores, model
+
+
+def _oracle_chunk_worker(job):
+    """One host core's share of the all-cores baseline: the oracle's whole
+    path on rows chunk*CHUNK .. of the workload (drawn here, untimed)."""
+    wname, chunk, rows = job
+    sys.path.insert(0, ROOT)
+    from paper_1402_6964_gb300 import synth
+    w = synth.WORKLOADS[wname]
+    P = synth.planted_structure(w.n, w.r, w.seed, w.alpha, w.decades)
+    X = synth.rows_chunk(P, w.seed, chunk, rows, w.noise, w.w_dist)
+    return cpu_oracle_step(X, w, rows)
+
+
+def cpu_baseline_all_cores(wname: str, rows: int, cores: int):
+    """The oracle as it stands on every host core at once: `cores` spawned
+    processes, each running the whole path on its own `rows`-row chunk of the
+    workload; GB/s = all rows / wall time of the slowest."""
+    import multiprocessing as mp
+    from paper_1402_6964_gb300 import synth
+    w = synth.WORKLOADS[wname]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_chunk_worker, [(wname, c, 2000) for c in range(cores)])  # start-up, page-in
+        t0 = time.perf_counter()
+        secs = pool.map(_oracle_chunk_worker, [(wname, c, rows) for c in range(cores)])
+        wall = time.perf_counter() - t0
+    return {"value": 4.0 * rows * w.n * cores / wall / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes, each the whole path on its own {rows}-row chunk of the workload; "
+                      f"wall {wall:.1f} s (slowest process {max(secs):.1f} s)"}
 
 
 def time_over_ranks(t_local: float, world: int, device=None) -> float:
@@ -536,7 +678,7 @@ def run_ours(args):
     # metric's "mixed vs FP32 at stated R error"), same resident X
     forms = {}
     for form in ("fp32", "tf32x3"):
-        if form == "tf32x3" and not (16 < n <= 64 and k <= 32):
+        if form == "tf32x3" and not tc_form_available(n, k):
             continue
         Rf = torch.empty((n, n), dtype=torch.float64, device=dev)
         csf = torch.empty(n, dtype=torch.float64, device=dev)
@@ -575,9 +717,35 @@ def run_ours(args):
         rows = args.cpu_rows
         Xh = X if X is not None else Xd[:rows].cpu().numpy()
         tcpu = cpu_oracle_step(Xh, w, rows)
-        cpu = {"value": 4.0 * rows * n / tcpu / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+        one = {"value": 4.0 * rows * n / tcpu / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"first {rows} rows of the workload (pass + SPA/XRAY/GP + NNLS + residual), "
                          f"{tcpu:.1f} s"}
+        ncores, model = host_cpu_info()
+        cpu = one
+        if ncores > 1:
+            try:
+                cpu = cpu_baseline_all_cores(args.workload, args.cpu_rows_per_core, ncores)
+                cpu["single_core"] = one
+            except Exception as ex:  # the one-core figure stands alone
+                one["all_cores_error"] = str(ex)[:200]
+        cpu["nproc"] = ncores
+        cpu["cpu_model"] = model
+
+    # ---- the other workloads of the metric, measured after the main one
+    other = None
+    if rank == 0 and world == 1 and not args.no_other and args.rows is None:
+        del Xd
+        torch.cuda.empty_cache()
+        other = {}
+        for name, fn in (("illcond_1e8x200_forms", run_illcond_forms), ("fc_stream_1p6e9x25", run_stream),
+                         ("batch_256", run_batched)):
+            try:
+                sub = argparse.Namespace(**vars(args))
+                sub.rows, sub.steps, sub.warmup = None, 3, 3
+                sub.workload = "fc_stream_1p6e9x25"
+                other[name] = fn(sub, quiet=True)
+            except Exception as ex:
+                other[name] = {"error": str(ex)[:300]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -591,7 +759,7 @@ def run_ours(args):
                 "leaf_ms": statistics.mean(leaf_ms), "r_error": r_err,
                 "K_spa": K_spa, "K_planted": P.K.tolist(), "forms": forms,
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "cpu_baseline": cpu,
-                "wall_s_timed": t_wall}
+                "wall_s_timed": t_wall, "other_configs": other}
         print(json.dumps(line), flush=True)
     h.close()
     if world > 1:
@@ -604,9 +772,10 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["step", "gp", "batched", "stream"], default="step",
+    ap.add_argument("--mode", choices=["step", "gp", "batched", "stream", "illcond"], default="step",
                     help="step: the whole hot path (default); gp: the projection-only pass; "
-                         "batched: 256 independent problems; stream: 1.6e9 x 25 in 64M-row chunks")
+                         "batched: 256 independent problems; stream: 1.6e9 x 25 in 64M-row chunks; "
+                         "illcond: the 1e8 x 200 workload in each arithmetic form")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--prec", choices=["auto", "fp32", "tf32x3"], default="auto")
     ap.add_argument("--workload", default=WORKLOAD)
@@ -615,7 +784,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--eager", action="store_true", help="launch the selection chains eagerly (no CUDA graph)")
     ap.add_argument("--cpu-rows", type=int, default=1_000_000)
-    ap.add_argument("--ref-rows", type=int, default=250_000)
+    ap.add_argument("--cpu-rows-per-core", type=int, default=500_000,
+                    help="rows per process of the all-cores oracle baseline")
+    ap.add_argument("--no-other", action="store_true",
+                    help="skip the 1e8 x 200 forms, the 1.6e9 x 25 stream and the 256-problem batch")
+    ap.add_argument("--ref-rows", type=int, default=250_000, help="rows per process and step of --impl reference")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -627,6 +800,8 @@ def main():
         run_batched(args)
     elif args.mode == "stream":
         run_stream(args)
+    elif args.mode == "illcond":
+        run_illcond_forms(args)
     else:
         run_ours(args)
 
