@@ -10,8 +10,9 @@
 // compact-WY form (Schreiber and Van Loan, SIAM J. Sci. Stat. Comput. 10,
 // 1989), one 16-column panel P = j0 .. j0+15 at a time:
 //
-//   1. the panel of [R; A] is factored on the SIMT cores by one warp, lane
-//      (c, h) holding column j0+c of tile rows 64h .. 64h+63: reflectors
+//   1. the panel of [R; A] is factored on the SIMT cores by all four warps,
+//      lane (c, h) of warp w holding column j0+c of 16 tile rows, the warps'
+//      partial dot products summed through shared memory: reflectors
 //      v_q = [e_(j0+q); y_q] with the same column step as the SIMT leaves
 //      (beta = -sign(alpha) sqrt(alpha^2 + sigma), y = A(:,j) / (alpha -
 //      beta), tau = (beta - alpha) / beta); the lanes of finished columns
@@ -103,7 +104,8 @@ struct WyMap {
     static constexpr uint32_t oXP = up(oXS + XR * xld * 4, 16);  // panel columns / Y, 128 x kTld
     static constexpr uint32_t oRR = up(oXP + kRows * kTld * 4, 16);  // R rows j0 .. j0+15, 16 x NP
     static constexpr uint32_t oPub = oRR + kNB * NP * 4;  // published pivot column, 128 floats
-    static constexpr uint32_t oT = oPub + kRows * 4;      // T, 16 x 17
+    static constexpr uint32_t oRed = oPub + kRows * 4;    // per-warp partial dots: [step parity][4 warps][16]
+    static constexpr uint32_t oT = oRed + 2 * 4 * kNB * 4;  // T, 16 x 17
     static constexpr uint32_t oGy = oT + kNB * kTld * 4;  // Y'Y, 16 x 17
     static constexpr uint32_t oTau = oGy + kNB * kTld * 4;
     static constexpr uint32_t oBar = up(oTau + kNB * 4, 16);
@@ -284,27 +286,34 @@ __global__ void __launch_bounds__(kRows, NP <= 64 ? 2 : 1) tsqr_wy_kernel(const 
             }
             __syncthreads();
 
-            // ---- 1. panel factorization (warp 0): lane (c, h) holds column j0+c of rows 64h .. 64h+63
-            if (warp == 0) {
+            // ---- 1. panel factorization, all four warps: lane (c, h) of warp w holds
+            // column j0+c of tile rows 32w + 16h .. 32w + 16h + 15.  Each column step
+            // forms the warp's partial dot products with the published pivot, sums
+            // the two row halves with one xor shuffle and the four warps' partials
+            // through shared memory (one barrier per step, buffers alternating by
+            // step parity); every lane then applies the step to its own rows.
+            {
                 const int c = lane & 15, h = lane >> 4;
-                float av[64];
+                const int rb = 32 * warp + 16 * h;  // first tile row of this lane
+                float* red = reinterpret_cast<float*>(sm + M::oRed);
+                float av[16];
 #pragma unroll
-                for (int i = 0; i < 64; ++i) av[i] = XP[(64 * h + i) * kTld + c];
+                for (int i = 0; i < 16; ++i) av[i] = XP[(rb + i) * kTld + c];
                 for (int j = 0; j < pw; ++j) {
                     if (c == j) {
 #pragma unroll
-                        for (int i4 = 0; i4 < 16; ++i4)
-                            reinterpret_cast<float4*>(PUB)[16 * h + i4] =
+                        for (int i4 = 0; i4 < 4; ++i4)
+                            reinterpret_cast<float4*>(PUB)[rb / 4 + i4] =
                                 make_float4(av[4 * i4], av[4 * i4 + 1], av[4 * i4 + 2], av[4 * i4 + 3]);
                     }
                     const int jg = j0 + j;
                     const float alpha = RR[j * NP + jg];
                     const float rjc = RR[j * NP + j0 + c];
                     __syncwarp();
-                    float pv[64];
+                    float pv[16];
 #pragma unroll
-                    for (int i4 = 0; i4 < 16; ++i4) {
-                        const float4 v = reinterpret_cast<const float4*>(PUB)[16 * h + i4];
+                    for (int i4 = 0; i4 < 4; ++i4) {
+                        const float4 v = reinterpret_cast<const float4*>(PUB)[rb / 4 + i4];
                         pv[4 * i4] = v.x;
                         pv[4 * i4 + 1] = v.y;
                         pv[4 * i4 + 2] = v.z;
@@ -312,7 +321,7 @@ __global__ void __launch_bounds__(kRows, NP <= 64 ? 2 : 1) tsqr_wy_kernel(const 
                     }
                     float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
 #pragma unroll
-                    for (int i = 0; i < 64; i += 4) {
+                    for (int i = 0; i < 16; i += 4) {
                         g0 = fmaf(pv[i], av[i], g0);
                         g1 = fmaf(pv[i + 1], av[i + 1], g1);
                         g2 = fmaf(pv[i + 2], av[i + 2], g2);
@@ -320,6 +329,10 @@ __global__ void __launch_bounds__(kRows, NP <= 64 ? 2 : 1) tsqr_wy_kernel(const 
                     }
                     float g = (g0 + g1) + (g2 + g3);
                     g += __shfl_xor_sync(FULL, g, 16);
+                    float* rj = red + (j & 1) * 4 * kNB;
+                    if (h == 0) rj[warp * kNB + c] = g;
+                    __syncthreads();
+                    g = (rj[c] + rj[kNB + c]) + (rj[2 * kNB + c] + rj[3 * kNB + c]);
                     const float sig = __shfl_sync(FULL, g, j);
                     if (sig > 0.f) {
                         const HhScalars hs = hh_scalars(alpha, sig);
@@ -327,19 +340,19 @@ __global__ void __launch_bounds__(kRows, NP <= 64 ? 2 : 1) tsqr_wy_kernel(const 
                             const float wp = fmaf(hs.d, rjc, g);  // d (R_jc + g_c / d)
                             const float f = (wp * hs.rd) * hs.rb;
 #pragma unroll
-                            for (int i = 0; i < 64; ++i) av[i] = fmaf(f, pv[i], av[i]);
-                            if (h == 0) RR[j * NP + j0 + c] = fmaf(wp, hs.rb, rjc);
+                            for (int i = 0; i < 16; ++i) av[i] = fmaf(f, pv[i], av[i]);
+                            if (warp == 0 && h == 0) RR[j * NP + j0 + c] = fmaf(wp, hs.rb, rjc);
                         } else if (c == j) {
 #pragma unroll
-                            for (int i = 0; i < 64; ++i) av[i] *= hs.rd;  // y_j = A(:,j) / (alpha - beta)
-                            if (h == 0) {
+                            for (int i = 0; i < 16; ++i) av[i] *= hs.rd;  // y_j = A(:,j) / (alpha - beta)
+                            if (warp == 0 && h == 0) {
                                 RR[j * NP + jg] = hs.beta;
                                 tau[j] = -hs.d * hs.rb;
                             }
-                        } else if (c < j && h == 0) {
+                        } else if (c < j && warp == 0 && h == 0) {
                             Gy[c * kTld + j] = g * hs.rd;  // y_c' y_j
                         }
-                    } else if (h == 0) {
+                    } else if (warp == 0 && h == 0) {
                         // nothing below R_jj: the identity (tau = 0, y_j = 0)
                         if (c == j) tau[j] = 0.f;
                         if (c < j) Gy[c * kTld + j] = 0.f;
@@ -348,41 +361,41 @@ __global__ void __launch_bounds__(kRows, NP <= 64 ? 2 : 1) tsqr_wy_kernel(const 
                 }
                 // Y into the panel buffer (rows of Y for the tensor-memory copy)
 #pragma unroll
-                for (int i = 0; i < 64; ++i) XP[(64 * h + i) * kTld + c] = av[i];
+                for (int i = 0; i < 16; ++i) XP[(rb + i) * kTld + c] = av[i];
                 if (ntr > 0) {
                     // Y' as GEMM1's B operand (row c, K = tile row), hi and lo
 #pragma unroll
-                    for (int i4 = 0; i4 < 16; ++i4) {
-                        const uint32_t off = sw128_off(c, 64 * h + 4 * i4, kNB / 8);
+                    for (int i4 = 0; i4 < 4; ++i4) {
+                        const uint32_t off = sw128_off(c, rb + 4 * i4, kNB / 8);
                         const float4 v = make_float4(av[4 * i4], av[4 * i4 + 1], av[4 * i4 + 2], av[4 * i4 + 3]);
                         *reinterpret_cast<float4*>(sm + M::oYsH + off) = v;
                         *reinterpret_cast<float4*>(sm + M::oYsL + off) =
                             make_float4(tc::tf32_lo(v.x), tc::tf32_lo(v.y), tc::tf32_lo(v.z), tc::tf32_lo(v.w));
                     }
-                    __syncwarp();
-                    if (lane < kNB) {
-                        // row i of T: T(i,i) = tau_i, T(i,q) = -tau_q sum_{i<=m<q} T(i,m) (Y'Y)(m,q)
-                        const int i = lane;
-                        float Ti[kNB];
-#pragma unroll
-                        for (int q = 0; q < kNB; ++q) {
-                            float v = 0.f;
-                            if (q == i) {
-                                v = tau[i];
-                            } else if (q > i) {
-                                float s = 0.f;
-#pragma unroll
-                                for (int m = 0; m < q; ++m)
-                                    if (m >= i) s = fmaf(Ti[m], Gy[m * kTld + q], s);
-                                v = -tau[q] * s;
-                            }
-                            Ti[q] = v;
-                        }
-#pragma unroll
-                        for (int q = 0; q < kNB; ++q) Ts[i * kTld + q] = Ti[q];
-                    }
                     tc::fence_async_smem();
                 }
+            }
+            __syncthreads();
+            if (ntr > 0 && warp == 0 && lane < kNB) {
+                // row i of T: T(i,i) = tau_i, T(i,q) = -tau_q sum_{i<=m<q} T(i,m) (Y'Y)(m,q)
+                const int i = lane;
+                float Ti[kNB];
+#pragma unroll
+                for (int q = 0; q < kNB; ++q) {
+                    float v = 0.f;
+                    if (q == i) {
+                        v = tau[i];
+                    } else if (q > i) {
+                        float s = 0.f;
+#pragma unroll
+                        for (int m = 0; m < q; ++m)
+                            if (m >= i) s = fmaf(Ti[m], Gy[m * kTld + q], s);
+                        v = -tau[q] * s;
+                    }
+                    Ti[q] = v;
+                }
+#pragma unroll
+                for (int q = 0; q < kNB; ++q) Ts[i * kTld + q] = Ti[q];
             }
             __syncthreads();
 
@@ -432,7 +445,9 @@ __global__ void __launch_bounds__(kRows, NP <= 64 ? 2 : 1) tsqr_wy_kernel(const 
                             }
                         }
                         block_sync();
-                        if (warp == 0) {
+                        // the MMAs are issued from warp 3: for n <= 96 it has no columns to
+                        // transpose, so the issue overlaps the other warps' next chunk
+                        if (warp == 3) {
                             if (tc::elect_one()) {
 #pragma unroll
                                 for (int ks = 0; ks < kCH / 8; ++ks) {
