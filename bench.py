@@ -423,6 +423,65 @@ def run_illcond_forms(args, quiet=False):
     return line
 
 
+def per_n_sweep(sms: int, mhz: float, hbm: float):
+    """The plain FP32 pass (k = 0, the metric's TSQR pass) at n = 8 .. 64 on
+    about 2 GB of uniform X drawn on the device: leaf time from the library's
+    events, GB/s, and the fraction of the HBM roofline and of the binary32
+    SIMT peak (2 n^2 flops per row)."""
+    import torch
+
+    from paper_1402_6964_gb300 import mrnmf
+    h = mrnmf.Handle()
+    out = {}
+    peak = _fp32_simt_peak_tflops(sms, mhz)
+    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0.record()
+    l1.record()
+    for n in (8, 16, 25, 32, 50, 64):
+        m = int(5e8 // n)
+        X = torch.rand(m, n, device="cuda")
+        for _ in range(3):
+            h.tsqr_r(X, prec="fp32")
+        h.sync()
+        h.profile_events(l0, l1)
+        reps, leaf = 5, 0.0
+        for _ in range(reps):
+            h.tsqr_r(X, prec="fp32")
+            torch.cuda.synchronize()
+            leaf += l0.elapsed_time(l1)
+        h.profile_events(None, None)
+        h.sync()
+        ms = leaf / reps
+        gbs = 4.0 * m * n / ms / 1e6
+        tf = 2.0 * m * n * n / ms / 1e9
+        out[str(n)] = {"m": m, "leaf_ms": ms, "GBps": gbs, "hbm_frac": gbs / hbm, "tflops": tf,
+                       "simt_frac": tf / peak}
+        del X
+    h.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def host_link():
+    """Pinned host -> device copy bandwidth (GB/s) at a few transfer sizes."""
+    import torch
+    out = {}
+    for mb in (64, 256, 1024):
+        hsrc = torch.empty(mb << 18, dtype=torch.float32).pin_memory()
+        d = torch.empty(mb << 18, dtype=torch.float32, device="cuda")
+        d.copy_(hsrc, non_blocking=True)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(5):
+            d.copy_(hsrc, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        out[f"{mb}MiB"] = 5 * (mb << 20) / a.elapsed_time(b) / 1e6
+        del hsrc, d
+    return out
+
+
 def host_cpu_info():
     """Core count and model of the host the oracle runs on (nproc, lscpu)."""
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
@@ -711,6 +770,10 @@ def run_ours(args):
                "d2h_bytes_per_step": int(4 * r + 8 * r * n + 16), "ms_per_step": te * 1e3,
                "call": "mrnmf_factorize_host (SPA, H, residual)"}
         del Xp
+        try:
+            e2e["host_link_h2d_GBps"] = host_link()
+        except Exception as ex:
+            e2e["host_link_h2d_GBps"] = {"error": str(ex)[:200]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -737,6 +800,10 @@ def run_ours(args):
         del Xd
         torch.cuda.empty_cache()
         other = {}
+        try:
+            other["per_n_fp32_pass"] = per_n_sweep(sms, mhz, hbm)
+        except Exception as ex:
+            other["per_n_fp32_pass"] = {"error": str(ex)[:300]}
         for name, fn in (("illcond_1e8x200_forms", run_illcond_forms), ("fc_stream_1p6e9x25", run_stream),
                          ("batch_256", run_batched)):
             try:
@@ -754,7 +821,9 @@ def run_ours(args):
                 "config": {"workload": w.name, "m": m, "n": n, "r": r, "k": k, "prec": args.prec,
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "selections": "eager, three streams" if graph is None else "CUDA graph, three streams",
-                           "l2": f"input ({bytes_step / 1e9:.2f} GB) larger than L2 (129 MB); no flush needed"},
+                           "l2": f"input ({bytes_step / 1e9:.2f} GB) larger than L2 (129 MB); no flush needed",
+                           "tune_file": os.path.relpath(os.environ["MRNMF_TUNE_FILE"], ROOT)
+                           if os.environ.get("MRNMF_TUNE_FILE") else None},
                 "roofline": roofline, "roofline_other": roof_alu if roofline is roof_hbm else roof_hbm,
                 "leaf_ms": statistics.mean(leaf_ms), "r_error": r_err,
                 "K_spa": K_spa, "K_planted": P.K.tolist(), "forms": forms,
@@ -766,7 +835,14 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+TUNE_FILE = os.path.join(ROOT, "paper_1402_6964_gb300", "tune_gb300.txt")
+
+
 def main():
+    # the library reads its tuning table from MRNMF_TUNE_FILE on first use;
+    # the committed table (paper_1402_6964_gb300/tune.py wrote it) is the default
+    if "MRNMF_TUNE_FILE" not in os.environ and os.path.exists(TUNE_FILE):
+        os.environ["MRNMF_TUNE_FILE"] = TUNE_FILE
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)

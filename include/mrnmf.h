@@ -356,6 +356,32 @@ mrnmf_status mrnmf_hh_scalars_selftest(const float* alpha, const float* sigma, i
 mrnmf_status mrnmf_wait_selftest(int32_t missing, int64_t limit_ns, int32_t* out, int32_t* status, void* stream);
 uint64_t mrnmf_kernel_launches(void);
 
+/*
+ * Tuning table (no counterpart in the paper; the paper's MapReduce runs leave
+ * the number of map tasks to Hadoop).  Process-wide, not per handle.  Plain
+ * text, one setting per line ('#' starts a comment):
+ *     pass  <n_lo> <n_hi> <log2m_lo> <log2m_hi> <stream_factor>
+ *     batch <family 1..3> <waves>
+ * A pass of n columns over m rows scales its default number of row streams
+ * (map tasks, Sec. 3.5) by the stream_factor of the first matching pass line
+ * (n_lo <= n <= n_hi, log2m_lo <= log2(m) < log2m_hi; factor in (0, 64]); a
+ * batched call plans family f's streams (1: n <= 32, 2: 33..64, 3: 65..128)
+ * for `waves` waves of resident CTAs (in [0.25, 256]).  Settings change only
+ * the amount of parallel work: R is the same up to rounding order.
+ * The table is read from the file named by MRNMF_TUNE_FILE when first needed
+ * (a malformed file is reported on stderr and ignored); paper_1402_6964_gb300/
+ * tune.py writes one from measurements.
+ * mrnmf_tune_load: replace the table with the file at `path` (NULL: clear
+ * it).  MRNMF_ERR_INVALID_ARG if the file is unreadable or a line is
+ * malformed (the table is then unchanged).  Host only; make no call that
+ * runs a pass concurrently with it.
+ * mrnmf_tune_query: the stream factor a pass of n columns over m rows would
+ * use, and (batch_waves, 3 doubles, nullable) each family's planned waves
+ * (0 = the built-in default).  Host only.
+ */
+mrnmf_status mrnmf_tune_load(const char* path);
+mrnmf_status mrnmf_tune_query(int32_t n, int64_t m, double* stream_factor, double* batch_waves);
+
 #ifdef __cplusplus
 }
 #endif

@@ -122,7 +122,7 @@ size_t plan_batched(const mrnmf_problem* pr, int count, int sms, int ctas_per_sm
         if (fam[i] < 0) continue;
         const int f = fam[i];
         const int L = fam_rows(f), spc = fam_spc(f);
-        const double waves = f < 2 ? 2.0 : kPipeWaves;
+        const double waves = tune_batch_waves(f + 1, f < 2 ? 2.0 : kPipeWaves);
         const double budget = waves * sms * ctas_per_sm[f] * spc;
         const double share = cost[f] > 0 ? fam_cost(f, pr[i]) / cost[f] : 1.0;
         int64_t s = (int64_t)(budget * share + 0.5);

@@ -45,6 +45,12 @@ bool tree64_supported(int n);
 // MRNMF_TREE64=1 selects it for binary32 passes.
 bool tree64_requested();
 
+// The tuning table (tune.cu): a factor on the stream count of a pass of n
+// columns over m rows (1 without an entry), and the waves a batch family's
+// streams are planned for (`dflt` without an entry).
+double tune_stream_factor(int n, int64_t m);
+double tune_batch_waves(int family, double dflt);
+
 // Number of streams for a pass over about `m` rows (0 = unknown / streaming).
 int choose_streams(int n, int k, int fp64, int tc, int64_t m);
 

@@ -20,6 +20,7 @@
 // R([X1; X2]) = R([R1; R2]) (Sec. 3.1) makes the result the R of all rows.
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 
@@ -373,7 +374,24 @@ void pass_state_carve(PassState& st, void* base)
     st.gx = reinterpret_cast<double*>(p);
 }
 
+static int choose_streams_default(int n, int k, int fp64, int tc, int64_t m);
+
+// The default count, scaled by the tuning table's factor for (n, m): the
+// warp leaf keeps a multiple of its streams per CTA.
 int choose_streams(int n, int k, int fp64, int tc, int64_t m)
+{
+    const int P0 = choose_streams_default(n, k, fp64, tc, m);
+    const double f = tune_stream_factor(n, m);
+    if (f == 1.0) return P0;
+    int P = std::max(1, (int)std::lround(P0 * f));
+    if (!fp64 && !tc && warp_leaf_supported(n, k)) {
+        const int w = warp_leaf_warps_per_cta();
+        P = std::max(w, (P + w - 1) / w * w);
+    }
+    return P;
+}
+
+static int choose_streams_default(int n, int k, int fp64, int tc, int64_t m)
 {
     if (tc && !fp64) {
         // one stream per CTA, as many CTAs as the SM holds at once

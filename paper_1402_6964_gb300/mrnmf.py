@@ -30,6 +30,7 @@ EXPORTS = [
     "mrnmf_profile_events", "mrnmf_kernel_launches", "mrnmf_tsqr_r_noalloc", "mrnmf_tc_selftest", "mrnmf_wait_selftest", "mrnmf_hh_scalars_selftest",
     "mrnmf_rank_sweep", "mrnmf_tsqr_r_batched", "mrnmf_gather_columns", "mrnmf_full_residual",
     "mrnmf_r_svd", "mrnmf_stream_state_size", "mrnmf_stream_state_save", "mrnmf_stream_state_load",
+    "mrnmf_tune_load", "mrnmf_tune_query",
 ]
 
 
@@ -89,6 +90,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mrnmf_stream_state_size": ([P, ctypes.POINTER(ctypes.c_size_t)], st),
             "mrnmf_stream_state_save": ([P, P, ctypes.c_size_t, P], st),
             "mrnmf_stream_state_load": ([P, P, ctypes.c_size_t, P], st),
+            "mrnmf_tune_load": ([ctypes.c_char_p], st),
+            "mrnmf_tune_query": ([i32, i64, P, P], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -144,6 +147,23 @@ def tsqr_r_noalloc(X, R, colsum=None, status=None, stream=None) -> int:
     m, n = X.shape
     return int(load().mrnmf_tsqr_r_noalloc(_ptr(X), m, n, X.stride(0), _ptr(R), _ptr(colsum), _ptr(status),
                                            _stream(stream)))
+
+
+def tune_load(path) -> int:
+    """mrnmf_tune_load: replace the process-wide tuning table with the file at
+    `path` (None clears it).  Returns the C status."""
+    return int(load().mrnmf_tune_load(None if path is None else os.fsencode(path)))
+
+
+def tune_query(n: int, m: int):
+    """mrnmf_tune_query: (stream factor for a pass of n columns over m rows,
+    [waves planned for batch families 1..3, 0 = built-in default])."""
+    f = ctypes.c_double(0.0)
+    w = (ctypes.c_double * 3)()
+    st = int(load().mrnmf_tune_query(n, m, ctypes.byref(f), w))
+    if st != OK:
+        raise MrnmfError(st, "tune query")
+    return f.value, list(w)
 
 
 def tc_selftest(A, B, kind="tf32x3", status=None, stream=None):

@@ -509,3 +509,28 @@ def test_binary64_tree_matches_oracle(oracle):
         assert rel_fro(Rg, Ro) <= R_TOL_FP32
         col = np.linalg.norm(Rg - Ro, axis=0) / np.linalg.norm(Ro, axis=0)
         assert np.max(col) < COL_TOL_ILLCOND
+
+
+def test_tuned_stream_counts_match_oracle(h, oracle, tmp_path):
+    """Tuning-table settings change only the amount of parallel work: with far
+    fewer and with more row streams than the default (pass lines), and with
+    other batch waves, R still matches the oracle within the FP32 bound."""
+    from paper_1402_6964_gb300 import mrnmf
+    cases = [(200_000, 50), (60_000, 200), (30_000, 12)]
+    try:
+        for factor in (0.125, 4.0):
+            path = tmp_path / f"t{factor}.txt"
+            path.write_text(f"pass 1 256 0 64 {factor}\nbatch 1 1\nbatch 2 4\nbatch 3 8\n")
+            assert mrnmf.tune_load(str(path)) == mrnmf.OK
+            for m, n in cases:
+                X = synth.random_nonneg(m, n, seed=m + n)
+                R, cs = h.tsqr_r(dev(X), prec="fp32")
+                h.sync()
+                assert rel_fro(host(R), oracle.qr_r(X.astype(np.float64))) <= R_TOL_FP32, (factor, m, n)
+            Xs = [synth.random_nonneg(m, n, seed=m * n) for m, n in [(50_000, 20), (40_000, 60), (30_000, 100)]]
+            outs = h.tsqr_r_batched([dev(X) for X in Xs])
+            h.sync()
+            for X, (R, cs) in zip(Xs, outs):
+                assert rel_fro(host(R), oracle.qr_r(X.astype(np.float64))) <= R_TOL_FP32
+    finally:
+        mrnmf.tune_load(None)
