@@ -361,13 +361,21 @@ uint64_t mrnmf_kernel_launches(void);
  * the number of map tasks to Hadoop).  Process-wide, not per handle.  Plain
  * text, one setting per line ('#' starts a comment):
  *     pass  <n_lo> <n_hi> <log2m_lo> <log2m_hi> <stream_factor>
+ *     rows  <n_lo> <n_hi> <k_lo> <k_hi> <tile_rows>
  *     batch <family 1..3> <waves>
  * A pass of n columns over m rows scales its default number of row streams
  * (map tasks, Sec. 3.5) by the stream_factor of the first matching pass line
- * (n_lo <= n <= n_hi, log2m_lo <= log2(m) < log2m_hi; factor in (0, 64]); a
+ * (n_lo <= n <= n_hi, log2m_lo <= log2(m) < log2m_hi; factor in (0, 64]).
+ * A binary32 pass on the warp leaf (n <= 64) with k projection rows (0
+ * without GX) stages tiles of the tile_rows of the first matching rows line
+ * (n_lo <= n <= n_hi, k_lo <= k <= k_hi; 32, 64 or 128), where the leaf's
+ * form for n has that height (n <= 32: 64 or 128; 33..64: 32 or 64) and its
+ * CTA fits in shared memory; otherwise the built-in height.  The variables
+ * MRNMF_WARP_ROWS1 (n <= 32) and MRNMF_WARP_ROWS (33..64) override it.  A
  * batched call plans family f's streams (1: n <= 32, 2: 33..64, 3: 65..128)
  * for `waves` waves of resident CTAs (in [0.25, 256]).  Settings change only
- * the amount of parallel work: R is the same up to rounding order.
+ * the amount and shape of the parallel work: R is the same up to rounding
+ * order.
  * The table is read from the file named by MRNMF_TUNE_FILE when first needed
  * (a malformed file is reported on stderr and ignored); paper_1402_6964_gb300/
  * tune.py writes one from measurements.
@@ -378,9 +386,14 @@ uint64_t mrnmf_kernel_launches(void);
  * mrnmf_tune_query: the stream factor a pass of n columns over m rows would
  * use, and (batch_waves, 3 doubles, nullable) each family's planned waves
  * (0 = the built-in default).  Host only.
+ * mrnmf_tune_leaf_rows: the tile height a binary32 pass of n columns with k
+ * projection rows would stage on the warp leaf, after the variables, the
+ * table and the default (0 where the warp leaf does not serve (n, k));
+ * MRNMF_ERR_INVALID_ARG for a NULL tile_rows, n < 1 or k < 0.  Host only.
  */
 mrnmf_status mrnmf_tune_load(const char* path);
 mrnmf_status mrnmf_tune_query(int32_t n, int64_t m, double* stream_factor, double* batch_waves);
+mrnmf_status mrnmf_tune_leaf_rows(int32_t n, int32_t k, int32_t* tile_rows);
 
 #ifdef __cplusplus
 }

@@ -50,6 +50,7 @@ bool tree64_requested();
 // streams are planned for (`dflt` without an entry).
 double tune_stream_factor(int n, int64_t m);
 double tune_batch_waves(int family, double dflt);
+int tune_leaf_rows(int n, int k);  // the table's warp-leaf tile height for (n, k); 0 without a `rows` line
 
 // Number of streams for a pass over about `m` rows (0 = unknown / streaming).
 int choose_streams(int n, int k, int fp64, int tc, int64_t m);

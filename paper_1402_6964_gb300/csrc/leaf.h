@@ -23,6 +23,7 @@ struct LeafArgs {
     uint64_t seed;
     int check;             // reject negative / NaN entries
     int* status;
+    int tile_rows;         // warp leaf: tile height the pass was planned with (0 = warp_leaf_rows_per_tile)
 };
 
 // Batched pass: one problem per entry, CTAs described one by one.

@@ -515,6 +515,7 @@ cudaError_t pass_push(PassState& st, const void* X, int64_t rows, int64_t ldx, i
         const int L = warp_leaf_rows_per_tile(st.n, a.gx ? st.k : 0);
         int64_t pw = (rows + st.P - 1) / st.P;
         a.rows_per_cta = ((pw + L - 1) / L) * L;
+        a.tile_rows = L;
         e = launch_warp_leaf(a, st.P, s);
         st.tri = st.P / warp_leaf_warps_per_cta();
     } else if (st.fp64) {

@@ -37,9 +37,8 @@ namespace {
 constexpr int kWarps = 4;  // streams per CTA
 constexpr int kFlush = 32;  // tiles between binary64 flushes of the partial sums
 
-// Tile heights: 64 rows when a lane owns one column (n <= 32), 32 rows when
-// it owns two (n <= 64): three 4-warp CTAs then fit per SM (measured faster
-// on GB300 than 64-row tiles with two CTAs; MRNMF_WARP_ROWS=64 selects those).
+// Tile heights: by default 64 rows when a lane owns one column (n <= 32), 32
+// rows when it owns two (n <= 64); leaf_rows() below says what can change that.
 
 __host__ __device__ inline int pk_row(int j, int n) { return j * n - (j * (j + 1)) / 2; }
 __host__ __device__ inline size_t up(size_t b, size_t a) { return (b + a - 1) / a * a; }
@@ -1006,30 +1005,40 @@ int ctas_per_sm_nc(int n, int k)
     return blocks < 1 ? 1 : blocks;
 }
 
-// Tile height of the two-column form (32, or 64 when MRNMF_WARP_ROWS=64).
-// Tile height of the one-column form (n <= 32).  Measured on GB300 (1.6e7
-// rows, with the split form for the last 16 columns): 64-row tiles are 3-7%
-// faster than 128-row ones with the projection (n = 16..28) and up to 8%
-// without it.  MRNMF_WARP_ROWS1=64|128 forces one height.
-int rows1(int n, int k)
+// Shared memory of one CTA of the warp leaf at tile height L; 0 where the form
+// serving n has no such height (one column per lane, n <= 32: 64 or 128 rows;
+// two columns per lane, 33..64: 32 or 64 rows).
+size_t warp_cta_smem(int n, int k, int L)
 {
-    (void)n;
-    (void)k;
-    static int forced = [] {
-        const char* e = getenv("MRNMF_WARP_ROWS1");
-        const int v = e ? atoi(e) : 0;
-        return (v == 64 || v == 128) ? v : 0;
-    }();
-    return forced ? forced : 64;
+    if (n <= 32) return L == 64 ? kWarps * warp_slice_bytes<64>(n, k) : L == 128 ? kWarps * warp_slice_bytes<128>(n, k) : 0;
+    return L == 32 ? kWarps * warp_slice_bytes<32>(n, k) : L == 64 ? kWarps * warp_slice_bytes<64>(n, k) : 0;
 }
 
-int rows2()
+constexpr size_t kWarpSmemCap = 220 * 1024;
+
+int env_rows(const char* name, int a, int b)
 {
-    static int v = [] {
-        const char* e = getenv("MRNMF_WARP_ROWS");
-        return (e && atoi(e) == 64) ? 64 : 32;
-    }();
-    return v;
+    const char* e = getenv(name);
+    const int v = e ? atoi(e) : 0;
+    return (v == a || v == b) ? v : 0;
+}
+
+// Tile height of the warp leaf for n columns and k projection rows (k = 0
+// without the projection).  In order: MRNMF_WARP_ROWS1=64|128 (n <= 32) or
+// MRNMF_WARP_ROWS=32|64 (33..64); the tuning table's `rows` line for (n, k);
+// the default.  Defaults, measured on GB300: the one-column form at 64 rows
+// ran 3-7% faster than at 128 with the projection (n = 16..28, 1.6e7 rows) and
+// up to 8% without it; the two-column form at 32 rows holds three or four CTAs
+// per SM.  A height whose CTA does not fit in shared memory gives the default.
+int leaf_rows(int n, int k)
+{
+    static const int f1 = env_rows("MRNMF_WARP_ROWS1", 64, 128);
+    static const int f2 = env_rows("MRNMF_WARP_ROWS", 32, 64);
+    const int dflt = n <= 32 ? 64 : 32;
+    int L = n <= 32 ? f1 : f2;
+    if (!L) L = tune_leaf_rows(n, k);
+    const size_t smem = L ? warp_cta_smem(n, k, L) : 0;
+    return (smem == 0 || smem > kWarpSmemCap) ? dflt : L;
 }
 
 }  // namespace
@@ -1046,21 +1055,20 @@ cudaError_t tree_wide_level(const float* Rin, int P_in, int n, float* Rout, cuda
 bool warp_leaf_supported(int n, int k)
 {
     if (n < 1 || n > 64 || k > 64) return false;
-    const size_t smem = (size_t)kWarps * (n <= 32 ? (rows1(n, k) == 128 ? warp_slice_bytes<128>(n, k) : warp_slice_bytes<64>(n, k))
-                                                  : (rows2() == 32 ? warp_slice_bytes<32>(n, k)
-                                                                   : warp_slice_bytes<64>(n, k)));
-    return smem <= 220 * 1024;
+    const size_t smem = warp_cta_smem(n, k, leaf_rows(n, k));
+    return smem > 0 && smem <= kWarpSmemCap;
 }
 
-int warp_leaf_rows_per_tile(int n, int k) { return n <= 32 ? rows1(n, k) : rows2(); }
+int warp_leaf_rows_per_tile(int n, int k) { return leaf_rows(n, k); }
 
 int warp_leaf_warps_per_cta() { return kWarps; }
 
 int warp_leaf_ctas_per_sm(int n, int k)
 {
-    if (n <= 32 && rows1(n, k) == 64) return k > 0 ? ctas_per_sm_nc<1, 64, true>(n, k) : ctas_per_sm_nc<1, 64, false>(n, k);
+    const int L = leaf_rows(n, k);
+    if (n <= 32 && L == 64) return k > 0 ? ctas_per_sm_nc<1, 64, true>(n, k) : ctas_per_sm_nc<1, 64, false>(n, k);
     if (n <= 32) return k > 0 ? ctas_per_sm_nc<1, 128, true>(n, k) : ctas_per_sm_nc<1, 128, false>(n, k);
-    if (rows2() == 32) return k > 0 ? ctas_per_sm_nc<2, 32, true>(n, k) : ctas_per_sm_nc<2, 32, false>(n, k);
+    if (L == 32) return k > 0 ? ctas_per_sm_nc<2, 32, true>(n, k) : ctas_per_sm_nc<2, 32, false>(n, k);
     return k > 0 ? ctas_per_sm_nc<2, 64, true>(n, k) : ctas_per_sm_nc<2, 64, false>(n, k);
 }
 
@@ -1130,10 +1138,12 @@ cudaError_t launch_tree_batched(const TreeCta* desc, int nctas, int family, cuda
 cudaError_t launch_warp_leaf(const LeafArgs& a, int streams, cudaStream_t s)
 {
     const bool gp = a.gx != nullptr && a.k > 0;
-    if (a.n <= 32 && rows1(a.n, gp ? a.k : 0) == 64)
-        return gp ? launch_nc<1, 64, true>(a, streams, s) : launch_nc<1, 64, false>(a, streams, s);
+    // the height rows_per_cta was rounded to, so that a table reloaded in between changes nothing
+    const int L = a.tile_rows ? a.tile_rows : leaf_rows(a.n, gp ? a.k : 0);
+    if (warp_cta_smem(a.n, gp ? a.k : 0, L) == 0 || a.rows_per_cta % L != 0) return cudaErrorInvalidValue;
+    if (a.n <= 32 && L == 64) return gp ? launch_nc<1, 64, true>(a, streams, s) : launch_nc<1, 64, false>(a, streams, s);
     if (a.n <= 32) return gp ? launch_nc<1, 128, true>(a, streams, s) : launch_nc<1, 128, false>(a, streams, s);
-    if (rows2() == 32) return gp ? launch_nc<2, 32, true>(a, streams, s) : launch_nc<2, 32, false>(a, streams, s);
+    if (L == 32) return gp ? launch_nc<2, 32, true>(a, streams, s) : launch_nc<2, 32, false>(a, streams, s);
     return gp ? launch_nc<2, 64, true>(a, streams, s) : launch_nc<2, 64, false>(a, streams, s);
 }
 

@@ -30,7 +30,7 @@ EXPORTS = [
     "mrnmf_profile_events", "mrnmf_kernel_launches", "mrnmf_tsqr_r_noalloc", "mrnmf_tc_selftest", "mrnmf_wait_selftest", "mrnmf_hh_scalars_selftest",
     "mrnmf_rank_sweep", "mrnmf_tsqr_r_batched", "mrnmf_gather_columns", "mrnmf_full_residual",
     "mrnmf_r_svd", "mrnmf_stream_state_size", "mrnmf_stream_state_save", "mrnmf_stream_state_load",
-    "mrnmf_tune_load", "mrnmf_tune_query",
+    "mrnmf_tune_load", "mrnmf_tune_query", "mrnmf_tune_leaf_rows",
 ]
 
 
@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mrnmf_stream_state_load": ([P, P, ctypes.c_size_t, P], st),
             "mrnmf_tune_load": ([ctypes.c_char_p], st),
             "mrnmf_tune_query": ([i32, i64, P, P], st),
+            "mrnmf_tune_leaf_rows": ([i32, i32, P], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -164,6 +165,16 @@ def tune_query(n: int, m: int):
     if st != OK:
         raise MrnmfError(st, "tune query")
     return f.value, list(w)
+
+
+def tune_leaf_rows(n: int, k: int = 0) -> int:
+    """mrnmf_tune_leaf_rows: tile height of the warp leaf for a binary32 pass
+    of n columns with k projection rows (0 where that leaf does not serve it)."""
+    r = ctypes.c_int32(0)
+    st = int(load().mrnmf_tune_leaf_rows(n, k, ctypes.byref(r)))
+    if st != OK:
+        raise MrnmfError(st, "tune leaf rows")
+    return r.value
 
 
 def tc_selftest(A, B, kind="tf32x3", status=None, stream=None):

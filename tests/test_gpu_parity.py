@@ -534,3 +534,32 @@ def test_tuned_stream_counts_match_oracle(h, oracle, tmp_path):
                 assert rel_fro(host(R), oracle.qr_r(X.astype(np.float64))) <= R_TOL_FP32
     finally:
         mrnmf.tune_load(None)
+
+
+@pytest.mark.parametrize("n,k,rows", [(20, 0, 128), (20, 12, 128), (50, 0, 64), (50, 20, 64), (60, 20, 64),
+                                      (64, 0, 64)])
+def test_tuned_tile_heights_match_oracle(h, oracle, tmp_path, n, k, rows):
+    """A rows line changes the warp leaf's tile height; R, the column sums and
+    G'X stay within the FP32 bounds of the oracle (m not a multiple of the
+    height, so every stream ends on a ragged tile)."""
+    from paper_1402_6964_gb300 import mrnmf
+    path = tmp_path / "rows.txt"
+    path.write_text(f"rows {n} {n} {k} {k} {rows}\n")
+    m = 150_001
+    X = synth.random_nonneg(m, n, seed=7 * n + k)
+    X64 = X.astype(np.float64)
+    try:
+        assert mrnmf.tune_load(str(path)) == mrnmf.OK
+        assert mrnmf.tune_leaf_rows(n, k) == rows
+        if k:
+            R, cs, GX = h.tsqr_gp(dev(X), k, seed=31, prec="fp32")
+        else:
+            R, cs = h.tsqr_r(dev(X), prec="fp32")
+        h.sync()
+    finally:
+        mrnmf.tune_load(None)
+    assert rel_fro(host(R), oracle.qr_r(X64)) <= R_TOL_FP32
+    np.testing.assert_allclose(host(cs), oracle.colsum(X64), rtol=1e-6)
+    if k:
+        GXo = oracle.gauss_project(X64, k, 31)
+        assert np.all(np.abs(host(GX) - GXo) <= 2e-6 * _gx_bound(X, k, 31) + 1e-12)

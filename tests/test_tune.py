@@ -1,6 +1,8 @@
 """The tuning table's file format and lookup (host only, no GPU): the first
-matching pass line gives the stream factor, batch lines the waves per family,
-a malformed file is rejected and leaves the table unchanged, NULL clears it."""
+matching pass line gives the stream factor, the first matching rows line the
+warp leaf's tile height where its form has that height and the CTA fits,
+batch lines the waves per family; a malformed file is rejected and leaves the
+table unchanged, NULL clears it."""
 import pytest
 
 
@@ -46,3 +48,46 @@ def test_missing_file_and_clear(mrnmf, tmp_path):
     assert mrnmf.tune_query(100, 10 ** 6)[0] == 3.0
     assert mrnmf.tune_load(None) == mrnmf.OK
     assert mrnmf.tune_query(100, 10 ** 6) == (1.0, [0.0, 0.0, 0.0])
+
+
+def test_rows_lines_pick_the_warp_leaf_tile_height(mrnmf, tmp_path):
+    # built-in heights: 64 rows for n <= 32 (one column per lane), 32 for 33..64
+    assert [mrnmf.tune_leaf_rows(n, k) for n, k in [(20, 0), (20, 12), (50, 0), (50, 20)]] == [64, 64, 32, 32]
+    assert mrnmf.tune_leaf_rows(100, 0) == 0   # not the warp leaf's
+    path = _write(tmp_path, "rows 33 64 0 0 64\nrows 1 32 0 64 128\nrows 1 64 0 64 32\n")
+    assert mrnmf.tune_load(path) == mrnmf.OK
+    assert mrnmf.tune_leaf_rows(50, 0) == 64   # first matching line
+    assert mrnmf.tune_leaf_rows(50, 20) == 32  # k = 20 outside [0, 0]: third line
+    assert mrnmf.tune_leaf_rows(20, 0) == 128
+    assert mrnmf.tune_leaf_rows(20, 12) == 128
+    assert mrnmf.tune_leaf_rows(100, 0) == 0
+
+
+def test_rows_line_the_form_cannot_take_gives_the_default(mrnmf, tmp_path):
+    # 32 rows is not a height of the one-column form, 128 not one of the two-column form
+    assert mrnmf.tune_load(_write(tmp_path, "rows 1 32 0 64 32\nrows 33 64 0 64 128\n")) == mrnmf.OK
+    assert mrnmf.tune_leaf_rows(20, 0) == 64
+    assert mrnmf.tune_leaf_rows(50, 0) == 32
+    # n = 64 with 64 projection rows: four 64-row slices need 232 KB of shared memory
+    assert mrnmf.tune_load(_write(tmp_path, "rows 33 64 0 64 64\n")) == mrnmf.OK
+    assert mrnmf.tune_leaf_rows(64, 0) == 64
+    assert mrnmf.tune_leaf_rows(64, 64) == 32
+
+
+@pytest.mark.parametrize("bad", ["rows 1 8 0 4 48\n", "rows 1 8 4 2 64\n", "rows 8 1 0 4 64\n",
+                                 "rows 1 8 -1 4 64\n", "rows 1 8 0 4\n"])
+def test_malformed_rows_line_is_rejected(mrnmf, tmp_path, bad):
+    assert mrnmf.tune_load(_write(tmp_path, "rows 1 64 0 64 64\n")) == mrnmf.OK
+    p = tmp_path / "bad.txt"
+    p.write_text(bad)
+    assert mrnmf.tune_load(str(p)) == mrnmf.ERR_INVALID_ARG
+    assert mrnmf.tune_leaf_rows(50, 0) == 64   # table unchanged
+
+
+def test_leaf_rows_query_rejects_bad_arguments(mrnmf):
+    import ctypes
+    lib = mrnmf.load()
+    r = ctypes.c_int32(0)
+    assert lib.mrnmf_tune_leaf_rows(0, 0, ctypes.byref(r)) == mrnmf.ERR_INVALID_ARG
+    assert lib.mrnmf_tune_leaf_rows(10, -1, ctypes.byref(r)) == mrnmf.ERR_INVALID_ARG
+    assert lib.mrnmf_tune_leaf_rows(10, 0, None) == mrnmf.ERR_INVALID_ARG
