@@ -203,6 +203,47 @@ def run_gp_pass(args):
     h.close()
 
 
+def run_pass(args):
+    """The plain binary32 TSQR pass (mrnmf_tsqr_r, k = 0) on uniform X of
+    --rows x --cols drawn on the device: pass and leaf time (library events),
+    GB/s of X and the fraction of the HBM roofline."""
+    import torch
+
+    from paper_1402_6964_gb300 import build, mrnmf
+
+    build.build()
+    m, n = args.rows or 10_000_000, args.cols
+    X = torch.rand(m, n, device="cuda")
+    h = mrnmf.Handle()
+    for _ in range(args.warmup):
+        h.tsqr_r(X, prec="fp32")
+    h.sync()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    l0, l1, a, b = ev(), ev(), ev(), ev()
+    l0.record()
+    l1.record()
+    h.profile_events(l0, l1)
+    tot = leaf = 0.0
+    for _ in range(args.steps):
+        a.record()
+        h.tsqr_r(X, prec="fp32")
+        b.record()
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+        leaf += l0.elapsed_time(l1)
+    h.profile_events(None, None)
+    h.sync()
+    hbm, _, src = _peaks()
+    ms, leaf_ms = tot / args.steps, leaf / args.steps
+    gbs = 4.0 * m * n / leaf_ms / 1e6
+    print(json.dumps({"mode": "pass", "metric": "TSQR pass GB/s of X (leaf)", "value": gbs, "unit": "GB/s",
+                      "ms_per_step": ms, "leaf_ms": leaf_ms, "steps": args.steps, "warmup": args.warmup,
+                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                   "frac": gbs / hbm, "peak_source": src},
+                      "config": {"workload": f"uniform {m}x{n}", "m": m, "n": n, "k": 0}}), flush=True)
+    h.close()
+
+
 def run_batched(args, quiet=False):
     """256 independent problems (m log-uniform in [1e4, 1e7], n uniform in
     10..128, r uniform in 3..min(16, n/2), sigma = 1e-3), drawn on the device:
@@ -424,7 +465,7 @@ def run_illcond_forms(args, quiet=False):
 
 
 def per_n_sweep(sms: int, mhz: float, hbm: float):
-    """The plain FP32 pass (k = 0, the metric's TSQR pass) at n = 8 .. 64 on
+    """The plain FP32 pass (k = 0, the metric's TSQR pass) at n = 4 .. 64 on
     about 2 GB of uniform X drawn on the device: leaf time from the library's
     events, GB/s, and the fraction of the HBM roofline and of the binary32
     SIMT peak (2 n^2 flops per row)."""
@@ -437,7 +478,7 @@ def per_n_sweep(sms: int, mhz: float, hbm: float):
     l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0.record()
     l1.record()
-    for n in (8, 16, 25, 32, 50, 64):
+    for n in (4, 8, 12, 16, 25, 32, 50, 64):
         m = int(5e8 // n)
         X = torch.rand(m, n, device="cuda")
         for _ in range(3):
@@ -848,14 +889,16 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["step", "gp", "batched", "stream", "illcond"], default="step",
+    ap.add_argument("--mode", choices=["step", "gp", "pass", "batched", "stream", "illcond"], default="step",
                     help="step: the whole hot path (default); gp: the projection-only pass; "
+                         "pass: the plain FP32 TSQR pass on uniform X of --rows x --cols; "
                          "batched: 256 independent problems; stream: 1.6e9 x 25 in 64M-row chunks; "
                          "illcond: the 1e8 x 200 workload in each arithmetic form")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--prec", choices=["auto", "fp32", "tf32x3"], default="auto")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--rows", type=int, default=None, help="first ROWS rows only (profiling a smaller case)")
+    ap.add_argument("--cols", type=int, default=8, help="columns of X in --mode pass")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--eager", action="store_true", help="launch the selection chains eagerly (no CUDA graph)")
@@ -872,6 +915,8 @@ def main():
         run_reference(args)
     elif args.mode == "gp":
         run_gp_pass(args)
+    elif args.mode == "pass":
+        run_pass(args)
     elif args.mode == "batched":
         run_batched(args)
     elif args.mode == "stream":

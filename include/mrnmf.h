@@ -366,8 +366,10 @@ uint64_t mrnmf_kernel_launches(void);
  * A pass of n columns over m rows scales its default number of row streams
  * (map tasks, Sec. 3.5) by the stream_factor of the first matching pass line
  * (n_lo <= n <= n_hi, log2m_lo <= log2(m) < log2m_hi; factor in (0, 64]).
- * A binary32 pass on the warp leaf (n <= 64) with k projection rows (0
- * without GX) stages tiles of the tile_rows of the first matching rows line
+ * A binary32 pass on the warp leaf (n <= 64; for n <= 16 only with k > 0,
+ * since the lane-group leaf with its fixed super-tiles serves k = 0) with k
+ * projection rows (0 without GX) stages tiles of the tile_rows of the first
+ * matching rows line
  * (n_lo <= n <= n_hi, k_lo <= k <= k_hi; 32, 64 or 128), where the leaf's
  * form for n has that height (n <= 32: 64 or 128; 33..64: 32 or 64) and its
  * CTA fits in shared memory; otherwise the built-in height.  The variables
@@ -388,7 +390,9 @@ uint64_t mrnmf_kernel_launches(void);
  * (0 = the built-in default).  Host only.
  * mrnmf_tune_leaf_rows: the tile height a binary32 pass of n columns with k
  * projection rows would stage on the warp leaf, after the variables, the
- * table and the default (0 where the warp leaf does not serve (n, k));
+ * table and the default, or the lane-group leaf's super-tile (32 * 64/S rows,
+ * S = 4, 8 or 16 lanes a stream) where that leaf serves (n, k); 0 where
+ * neither does;
  * MRNMF_ERR_INVALID_ARG for a NULL tile_rows, n < 1 or k < 0.  Host only.
  */
 mrnmf_status mrnmf_tune_load(const char* path);

@@ -59,6 +59,15 @@ cudaError_t launch_warp_batched(const BatchCta* desc, int nctas, const BatchProb
                                 int* status, cudaStream_t s);
 int warp_batched_rows_per_tile(int family);
 
+// Lane-group leaf (tsqr_group.cu): binary32, n <= 16, no projection; four
+// warps per CTA, one stream of the pass per warp (32/S Householder streams of
+// S lanes inside it, folded at the end of the launch).  The warp leaf's
+// functions dispatch to it; MRNMF_GROUP_LEAF=0 turns it off.
+bool group_leaf_supported(int n, int k);
+int group_leaf_rows_per_tile(int n);
+int group_leaf_ctas_per_sm(int n);
+cudaError_t launch_group_leaf(const LeafArgs& a, int streams, cudaStream_t s);
+
 // CTA-per-stream leaf (tsqr_warp.cu): binary32, 64 < n <= 256.
 bool cta_leaf_supported(int n, int k);
 int cta_leaf_rows_per_tile(int k, int n);

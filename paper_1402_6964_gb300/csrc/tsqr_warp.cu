@@ -1059,12 +1059,13 @@ bool warp_leaf_supported(int n, int k)
     return smem > 0 && smem <= kWarpSmemCap;
 }
 
-int warp_leaf_rows_per_tile(int n, int k) { return leaf_rows(n, k); }
+int warp_leaf_rows_per_tile(int n, int k) { return group_leaf_supported(n, k) ? group_leaf_rows_per_tile(n) : leaf_rows(n, k); }
 
 int warp_leaf_warps_per_cta() { return kWarps; }
 
 int warp_leaf_ctas_per_sm(int n, int k)
 {
+    if (group_leaf_supported(n, k)) return group_leaf_ctas_per_sm(n);
     const int L = leaf_rows(n, k);
     if (n <= 32 && L == 64) return k > 0 ? ctas_per_sm_nc<1, 64, true>(n, k) : ctas_per_sm_nc<1, 64, false>(n, k);
     if (n <= 32) return k > 0 ? ctas_per_sm_nc<1, 128, true>(n, k) : ctas_per_sm_nc<1, 128, false>(n, k);
@@ -1138,6 +1139,7 @@ cudaError_t launch_tree_batched(const TreeCta* desc, int nctas, int family, cuda
 cudaError_t launch_warp_leaf(const LeafArgs& a, int streams, cudaStream_t s)
 {
     const bool gp = a.gx != nullptr && a.k > 0;
+    if (group_leaf_supported(a.n, gp ? a.k : 0)) return launch_group_leaf(a, streams, s);
     // the height rows_per_cta was rounded to, so that a table reloaded in between changes nothing
     const int L = a.tile_rows ? a.tile_rows : leaf_rows(a.n, gp ? a.k : 0);
     if (warp_cta_smem(a.n, gp ? a.k : 0, L) == 0 || a.rows_per_cta % L != 0) return cudaErrorInvalidValue;

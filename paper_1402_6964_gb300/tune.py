@@ -114,6 +114,9 @@ def sweep_rows(h, reps, log):
                 else:
                     res[L] = _time(lambda: h.tsqr_r(X, prec="fp32"), reps, h.sync)
             dflt = heights[0]
+            if dflt not in res:
+                log(f"rows n={n} k={k}: another leaf serves this shape (its tile height is not tuned); skipped")
+                continue
 
             def again(L, k=k, n_lo=n_lo, n_hi=n_hi, k_lo=k_lo, k_hi=k_hi, X=X):
                 _with_table([f"rows {n_lo} {n_hi} {k_lo} {k_hi} {L}"])

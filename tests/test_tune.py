@@ -91,3 +91,13 @@ def test_leaf_rows_query_rejects_bad_arguments(mrnmf):
     assert lib.mrnmf_tune_leaf_rows(0, 0, ctypes.byref(r)) == mrnmf.ERR_INVALID_ARG
     assert lib.mrnmf_tune_leaf_rows(10, -1, ctypes.byref(r)) == mrnmf.ERR_INVALID_ARG
     assert lib.mrnmf_tune_leaf_rows(10, 0, None) == mrnmf.ERR_INVALID_ARG
+
+
+def test_lane_group_leaf_heights_are_fixed(mrnmf, tmp_path):
+    # n <= 16 without the projection runs on the lane-group leaf: super-tiles of
+    # 32 * 64/S rows (S = 4, 8, 16 lanes a stream), which rows lines do not change;
+    # with the projection the warp leaf serves those widths and follows the table
+    assert mrnmf.tune_load(_write(tmp_path, "rows 1 16 0 64 128\n")) == mrnmf.OK
+    assert [mrnmf.tune_leaf_rows(n, 0) for n in (1, 4, 5, 8, 9, 16)] == [512, 512, 256, 256, 128, 128]
+    assert mrnmf.tune_leaf_rows(8, 12) == 128
+    assert mrnmf.tune_leaf_rows(17, 0) == 64

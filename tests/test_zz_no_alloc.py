@@ -9,8 +9,8 @@ with different shapes (so stale contents of the shared array would show):
 * R against the oracle's FP64 Householder R within the FP32 pass tolerance
   (relative Frobenius 1e-5) and the column sums within relative 1e-6;
 * R and the column sums against the ordinary entry point mrnmf_tsqr_r;
-* shapes that reach each leaf: the warp leaf (n = 20, 50), the pipelined leaf
-  (n = 100), and n = 256, where the state of the usual stream count does not
+* shapes that reach each leaf: the lane-group leaf (n = 12), the warp leaf
+  (n = 20, 50), the pipelined leaf (n = 100), and n = 256, where the state of the usual stream count does not
   fit the array, so the call runs fewer streams and the fan-in-2 tree;
 * that a call allocates no device memory (torch's allocator and the driver's
   free-memory count do not grow across it);
@@ -33,7 +33,8 @@ R_TOL_FP32 = 1e-5     # relative Frobenius error of R, FP32 pass
 CS_RTOL = 1e-6        # column sums (binary64 partial sums of binary32 tile sums)
 
 # (m, n, seed, decades): decades > 0 scales the columns by 10^U(0, decades)
-CASES = [(300_001, 50, 1, 0.0), (70_003, 20, 2, 0.0), (200_000, 100, 3, 3.0), (40_000, 256, 4, 3.0)]
+CASES = [(300_001, 50, 1, 0.0), (70_003, 20, 2, 0.0), (200_000, 100, 3, 3.0), (40_000, 256, 4, 3.0),
+         (150_007, 12, 5, 0.0)]
 
 
 @pytest.fixture(scope="module")
