@@ -170,7 +170,8 @@ def run_reference(args):
 
 
 def run_gp_pass(args):
-    """Projection-only pass (mrnmf_gauss_project): GB/s of X, tensor-core or SIMT."""
+    """Projection-only pass: GB/s of X, SIMT (mrnmf_gauss_project) or a tensor-core
+    form (mrnmf_gauss_project_tc, --gp-form tf32x3 | bf16)."""
     import torch
 
     from paper_1402_6964_gb300 import build, mrnmf, synth
@@ -180,14 +181,18 @@ def run_gp_pass(args):
     X, _ = synth.workload_matrix(w, m=args.rows)
     Xd = torch.from_numpy(X).cuda()
     h = mrnmf.Handle()
+    if args.gp_form == "simt":
+        proj = lambda: h.gauss_project(Xd, w.k, w.seed)
+    else:
+        proj = lambda: h.gauss_project_tc(Xd, w.k, w.seed, form=args.gp_form)
     for _ in range(args.warmup):
-        h.gauss_project(Xd, w.k, w.seed)
+        proj()
     h.sync()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a.record()
     for _ in range(args.steps):
-        h.gauss_project(Xd, w.k, w.seed)
+        proj()
     b.record()
     torch.cuda.synchronize()
     h.sync()
@@ -196,7 +201,8 @@ def run_gp_pass(args):
     gbs = 4.0 * X.shape[0] * X.shape[1] / ms / 1e6
     print(json.dumps({"mode": "gp", "metric": "Gaussian projection pass GB/s of X", "value": gbs, "unit": "GB/s",
                       "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
-                      "path": "tcgen05 tf32x3" if os.environ.get("MRNMF_GP_TC") == "1" else "simt",
+                      "path": ("tcgen05 " + args.gp_form) if args.gp_form != "simt"
+                      else ("tcgen05 tf32x3" if os.environ.get("MRNMF_GP_TC") == "1" else "simt"),
                       "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                                    "frac": gbs / hbm, "peak_source": src},
                       "config": {"workload": w.name, "m": X.shape[0], "n": w.n, "k": w.k}}), flush=True)
@@ -899,6 +905,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--rows", type=int, default=None, help="first ROWS rows only (profiling a smaller case)")
     ap.add_argument("--cols", type=int, default=8, help="columns of X in --mode pass")
+    ap.add_argument("--gp-form", choices=["simt", "tf32x3", "bf16"], default="simt",
+                    help="--mode gp: the SIMT projection, or mrnmf_gauss_project_tc in a tensor-core form")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--eager", action="store_true", help="launch the selection chains eagerly (no CUDA graph)")

@@ -55,14 +55,23 @@ typedef enum {
 typedef enum { MRNMF_F32 = 0, MRNMF_F64 = 1 } mrnmf_dtype;
 
 /* Arithmetic of the pass.  FP64: everything in binary64 (X must be F64).
- * FP32: binary32 SIMT Householder.  TF32X3 (F32 input, 16 < n <= 64,
- * k <= 32, else MRNMF_ERR_INVALID_ARG): binary32 reflectors in 16-column
- * panels with the compact-WY trailing update and the Gaussian projection on
- * tcgen05 tensor cores in 3-pass split TF32 (hi*hi + hi*lo + lo*hi), FP32
- * accumulation; R within 1e-5 of the FP64 oracle but about 50x the FP32
- * form's error, and slower than FP32 on GB300, so AUTO does not pick it.
- * AUTO picks FP64 for F64 input, otherwise FP32. */
-typedef enum { MRNMF_PREC_AUTO = 0, MRNMF_PREC_FP64 = 1, MRNMF_PREC_FP32 = 2, MRNMF_PREC_TF32X3 = 3 } mrnmf_prec;
+ * FP32: binary32 SIMT Householder.  TF32X3 (F32 input, 16 < n <= 256, k <= 32
+ * for n <= 64 and k <= 48 above, else MRNMF_ERR_INVALID_ARG): binary32
+ * reflectors in 16-column panels with the compact-WY trailing update and the
+ * Gaussian projection on tcgen05 tensor cores in 3-pass split TF32
+ * (hi*hi + hi*lo + lo*hi, the main term and the corrections accumulated
+ * apart in FP32); R within 1e-5 of the FP64 oracle, slower than FP32 on
+ * GB300, so AUTO does not pick it.  AUTO picks FP64 for F64 input, otherwise
+ * FP32.  BF16 is a form of the projection alone (mrnmf_gauss_project_tc):
+ * G and X rounded to bfloat16, exact products, FP32 accumulation; the passes
+ * that form R reject it. */
+typedef enum {
+    MRNMF_PREC_AUTO = 0,
+    MRNMF_PREC_FP64 = 1,
+    MRNMF_PREC_FP32 = 2,
+    MRNMF_PREC_TF32X3 = 3,
+    MRNMF_PREC_BF16 = 4
+} mrnmf_prec;
 
 typedef enum { MRNMF_SPA = 0, MRNMF_XRAY = 1, MRNMF_GP = 2 } mrnmf_method;
 
@@ -107,6 +116,27 @@ mrnmf_status mrnmf_tsqr_r(mrnmf_handle* handle, const void* X, int64_t m, int32_
 mrnmf_status mrnmf_gauss_project(mrnmf_handle* handle, const void* X, int64_t m, int32_t n, int64_t ldx,
                                  int32_t dtype, int32_t k, uint64_t seed, int64_t row_offset,
                                  double* GX, double* colsum, void* stream);
+
+/*
+ * The same projection with G^T X on the tcgen05 tensor cores in a named form
+ * (Sec. 2.3 and Algorithm 1; the arithmetic form is this library's choice):
+ *   form = MRNMF_PREC_TF32X3: split TF32, hi*hi + hi*lo + lo*hi, FP32
+ *          accumulation (about binary32 accuracy);
+ *   form = MRNMF_PREC_BF16:   every entry of G and of X rounded to bfloat16
+ *          (round to nearest even) before the product; each product is then
+ *          exact in FP32 and the sums are FP32 accumulations, so GX equals
+ *          G_bf16^T X_bf16 up to FP32 summation error (binary64 across CTAs).
+ * G is the Gaussian matrix of mrnmf_gauss_project (same seed and row keys).
+ * The column sums are of X as read (binary32 tile sums, binary64 across).
+ *   X      device, F32, m-by-n row-major, ldx >= n; n <= 128 and 1 <= k <= 64
+ *   GX     device, k*n doubles out;  colsum device, n doubles out (nullable)
+ * MRNMF_ERR_INVALID_ARG for another form, n > 128, k outside [1, 64], or the
+ * argument errors of mrnmf_gauss_project.  A negative or NaN entry of X sets
+ * MRNMF_ERR_BAD_INPUT on the device.
+ */
+mrnmf_status mrnmf_gauss_project_tc(mrnmf_handle* handle, const float* X, int64_t m, int32_t n, int64_t ldx,
+                                    int32_t k, uint64_t seed, int64_t row_offset, int32_t form, double* GX,
+                                    double* colsum, void* stream);
 
 /*
  * The one-pass form of Sec. 3.5: R, the column sums and (if k > 0) GX from a

@@ -122,11 +122,12 @@ mrnmf_status setup_pass(mrnmf_handle* h, int n, int dtype, int prec, int k, uint
 
 mrnmf_status run_pass(mrnmf_handle* h, const void* X, int64_t m, int32_t n, int64_t ldx, int32_t dtype, int32_t prec,
                       int qr, double* R, double* colsum, int32_t k, uint64_t seed, int64_t row_offset, double* GX,
-                      cudaStream_t s)
+                      cudaStream_t s, int gp_form)
 {
     mrnmf_status st = setup_pass(h, n, dtype, prec, k, seed, m);
     if (st != MRNMF_OK) return st;
     h->st.rows_seen = row_offset;
+    h->st.gp_form = gp_form;
     cudaError_t e = mrnmf::pass_reset(h->st, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "pass reset");
     e = mrnmf::pass_push(h->st, X, m, ldx, dtype == MRNMF_F64, qr, h->d_status, s);
@@ -231,6 +232,23 @@ mrnmf_status mrnmf_gauss_project(mrnmf_handle* h, const void* X, int64_t m, int3
     const int prec = dtype == MRNMF_F64 ? MRNMF_PREC_FP64 : MRNMF_PREC_FP32;
     return run_pass(h, X, m, n, ldx, dtype, prec, 0, nullptr, colsum, k, seed, row_offset, GX,
                     static_cast<cudaStream_t>(stream));
+}
+
+mrnmf_status mrnmf_gauss_project_tc(mrnmf_handle* h, const float* X, int64_t m, int32_t n, int64_t ldx, int32_t k,
+                                    uint64_t seed, int64_t row_offset, int32_t form, double* GX, double* colsum,
+                                    void* stream)
+{
+    MRNMF_TRACE("mrnmf_gauss_project_tc");
+    mrnmf_status s = check_pass_args(h, X, m, n, ldx, MRNMF_F32, MRNMF_PREC_AUTO, k);
+    if (s != MRNMF_OK) return s;
+    if (k < 1 || !GX) return fail(h, MRNMF_ERR_INVALID_ARG, "need k >= 1 and GX");
+    if (row_offset < 0) return fail(h, MRNMF_ERR_INVALID_ARG, "row_offset < 0");
+    if (form != MRNMF_PREC_TF32X3 && form != MRNMF_PREC_BF16)
+        return fail(h, MRNMF_ERR_INVALID_ARG, "form must be MRNMF_PREC_TF32X3 or MRNMF_PREC_BF16");
+    if (!mrnmf::gp_tc_supported(n, k)) return fail(h, MRNMF_ERR_INVALID_ARG, "tensor-core projection needs n <= 128");
+    if ((s = bind_device(h)) != MRNMF_OK) return s;
+    return run_pass(h, X, m, n, ldx, MRNMF_F32, MRNMF_PREC_FP32, 0, nullptr, colsum, k, seed, row_offset, GX,
+                    static_cast<cudaStream_t>(stream), form);
 }
 
 mrnmf_status mrnmf_tsqr_gp(mrnmf_handle* h, const void* X, int64_t m, int32_t n, int64_t ldx, int32_t dtype,

@@ -57,7 +57,7 @@ mrnmf_status bind_device(mrnmf_handle* h);
 mrnmf_status grow(mrnmf_handle* h, void** buf, size_t* have, size_t need, const char* what);
 mrnmf_status run_pass(mrnmf_handle* h, const void* X, int64_t m, int32_t n, int64_t ldx, int32_t dtype, int32_t prec,
                       int qr, double* R, double* colsum, int32_t k, uint64_t seed, int64_t row_offset, double* GX,
-                      cudaStream_t s);
+                      cudaStream_t s, int gp_form = 0);
 
 }  // namespace api
 }  // namespace mrnmf

@@ -26,6 +26,8 @@ struct PassState {
     int fp64 = 0;       // 1: triangles and reflectors in binary64, else binary32
     int tc = 0;         // 1: tensor-core (TF32x3) leaf
     int tree64 = 0;     // 1: binary32 leaf triangles reduced by a binary64 tree
+    int gp_form = 0;    // projection-only pass on tcgen05: MRNMF_PREC_TF32X3 or MRNMF_PREC_BF16
+                        // (0: SIMT, or TF32X3 with MRNMF_GP_TC=1)
     void* R = nullptr;      // P * n * n (dense row-major, zeros below diag), T = float or double
     void* Rtmp = nullptr;   // ceil(P/2) * n * n binary64, ping-pong buffer of the tree
     double* cs = nullptr;   // P * n partial column sums
@@ -87,7 +89,8 @@ bool tc_preferred(int n, int k);   // and MRNMF_PREC_AUTO picks it
 
 // ---- tensor-core Gaussian projection pass (gp_tc.cu) ----
 bool gp_tc_supported(int n, int k);
+// bf16 = 1: bfloat16 operands (MRNMF_PREC_BF16), else split TF32 (MRNMF_PREC_TF32X3).
 cudaError_t launch_gp_tc(const float* X, int64_t rows, int64_t ldx, int n, int k, int64_t row_base, uint64_t seed,
-                         int max_ctas, double* cs, double* gx, int* status, cudaStream_t s);
+                         int max_ctas, double* cs, double* gx, int* status, int bf16, cudaStream_t s);
 
 }  // namespace mrnmf

@@ -487,15 +487,17 @@ cudaError_t pass_push(PassState& st, const void* X, int64_t rows, int64_t ldx, i
     // The projection-only pass runs on SIMT cores by default: G's generation
     // (Philox + Box-Muller), not the k-by-n product, dominates it, and the
     // tcgen05 form measured slower on GB300 (525 vs 727 GB/s at 1e7 x 50, k = 20).
-    // MRNMF_GP_TC=1 selects the tcgen05 (3-pass TF32) form.
+    // MRNMF_GP_TC=1 selects the tcgen05 (3-pass TF32) form; mrnmf_gauss_project_tc
+    // names a tcgen05 form explicitly (st.gp_form).
     static const bool gp_tc = [] {
         const char* v = getenv("MRNMF_GP_TC");
         return v && v[0] == '1';
     }();
-    if (!qr && !st.fp64 && !xf64 && st.k > 0 && gp_tc && gp_tc_supported(st.n, st.k)) {
+    const int gp_form = st.gp_form ? st.gp_form : (gp_tc ? MRNMF_PREC_TF32X3 : 0);
+    if (!qr && !st.fp64 && !xf64 && st.k > 0 && gp_form && gp_tc_supported(st.n, st.k)) {
         // projection-only pass on the tensor cores
         e = launch_gp_tc(static_cast<const float*>(X), rows, ldx, st.n, st.k, st.rows_seen, st.seed, st.P, st.cs,
-                         st.gx, status, s);
+                         st.gx, status, gp_form == MRNMF_PREC_BF16, s);
     } else if (st.tc && !xf64 && qr) {
         const int L = tc_leaf_rows_per_tile();
         int64_t pw = (rows + st.P - 1) / st.P;

@@ -20,12 +20,12 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmrnmf.so")
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NO_MEMORY, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_BAD_INPUT, ERR_RANK_DEFICIENT = range(8)
 F32, F64 = 0, 1
-PREC = {"auto": 0, "fp64": 1, "fp32": 2, "tf32x3": 3}
+PREC = {"auto": 0, "fp64": 1, "fp32": 2, "tf32x3": 3, "bf16": 4}
 METHOD = {"spa": 0, "xray": 1, "gp": 2}
 
 EXPORTS = [
     "mrnmf_create", "mrnmf_destroy", "mrnmf_last_error_string", "mrnmf_sync_status", "mrnmf_tsqr_r",
-    "mrnmf_gauss_project", "mrnmf_tsqr_gp", "mrnmf_select_extreme", "mrnmf_nnls_h", "mrnmf_residual",
+    "mrnmf_gauss_project", "mrnmf_gauss_project_tc", "mrnmf_tsqr_gp", "mrnmf_select_extreme", "mrnmf_nnls_h", "mrnmf_residual",
     "mrnmf_stream_begin", "mrnmf_stream_push", "mrnmf_stream_end", "mrnmf_factorize_host",
     "mrnmf_profile_events", "mrnmf_kernel_launches", "mrnmf_tsqr_r_noalloc", "mrnmf_tc_selftest", "mrnmf_wait_selftest", "mrnmf_hh_scalars_selftest",
     "mrnmf_rank_sweep", "mrnmf_tsqr_r_batched", "mrnmf_gather_columns", "mrnmf_full_residual",
@@ -68,6 +68,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "mrnmf_sync_status": ([P, P], st),
             "mrnmf_tsqr_r": ([P, P, i64, i32, i64, i32, i32, P, P, P], st),
             "mrnmf_gauss_project": ([P, P, i64, i32, i64, i32, i32, u64, i64, P, P, P], st),
+            "mrnmf_gauss_project_tc": ([P, P, i64, i32, i64, i32, u64, i64, i32, P, P, P], st),
             "mrnmf_tsqr_gp": ([P, P, i64, i32, i64, i32, i32, P, P, i32, u64, P, P], st),
             "mrnmf_select_extreme": ([P, i32, P, i32, P, P, i32, i32, P, P, P], st),
             "mrnmf_nnls_h": ([P, P, i32, P, i32, P, P], st),
@@ -277,6 +278,17 @@ class Handle:
         cs = torch.empty(n, dtype=torch.float64, device=X.device)
         self.check(self._lib.mrnmf_gauss_project(self.h, _ptr(X), m, n, X.stride(0), _dtype_code(X), k, seed,
                                                  row_offset, _ptr(GX), _ptr(cs), _stream(stream)))
+        return GX, cs
+
+    def gauss_project_tc(self, X, k, seed, form="bf16", row_offset=0, stream=None):
+        """mrnmf_gauss_project_tc: G'X on the tensor cores, form "bf16" or "tf32x3"."""
+        import torch
+        _check_X(X)
+        m, n = X.shape
+        GX = torch.empty((k, n), dtype=torch.float64, device=X.device)
+        cs = torch.empty(n, dtype=torch.float64, device=X.device)
+        self.check(self._lib.mrnmf_gauss_project_tc(self.h, _ptr(X), m, n, X.stride(0), k, seed, row_offset,
+                                                    PREC[form], _ptr(GX), _ptr(cs), _stream(stream)))
         return GX, cs
 
     def tsqr_gp(self, X, k, seed, prec="auto", stream=None, out=None):

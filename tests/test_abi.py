@@ -52,6 +52,14 @@ def test_argument_errors_need_no_device(lib):
     assert lib.mrnmf_tsqr_r(h, dummy, 1000, 8, 8, 0, 9, dummy, None, None) == mrnmf.ERR_INVALID_ARG
     assert lib.mrnmf_gauss_project(h, dummy, 1000, 8, 8, 0, 0, 1, 0, dummy, None, None) == mrnmf.ERR_INVALID_ARG
     assert lib.mrnmf_gauss_project(h, dummy, 1000, 8, 8, 0, 65, 1, 0, dummy, None, None) == mrnmf.ERR_INVALID_ARG
+    # tensor-core projection: a form other than TF32X3 / BF16, n > 128, k = 0, no GX
+    for form in (0, 1, 2, 5):
+        assert lib.mrnmf_gauss_project_tc(h, dummy, 1000, 8, 8, 4, 1, 0, form, dummy, None, None) == mrnmf.ERR_INVALID_ARG
+    assert lib.mrnmf_gauss_project_tc(h, dummy, 1000, 129, 129, 4, 1, 0, 4, dummy, None, None) == mrnmf.ERR_INVALID_ARG
+    assert lib.mrnmf_gauss_project_tc(h, dummy, 1000, 8, 8, 0, 1, 0, 4, dummy, None, None) == mrnmf.ERR_INVALID_ARG
+    assert lib.mrnmf_gauss_project_tc(h, dummy, 1000, 8, 8, 4, 1, 0, 4, None, None, None) == mrnmf.ERR_INVALID_ARG
+    # BF16 is a form of the projection alone: the passes that form R reject it
+    assert lib.mrnmf_tsqr_r(h, dummy, 1000, 8, 8, 0, 4, dummy, None, None) == mrnmf.ERR_INVALID_ARG
     # selection: r > n, unknown method, GP without GX
     assert lib.mrnmf_select_extreme(h, 0, dummy, 8, dummy, None, 0, 9, dummy, None, None) == mrnmf.ERR_INVALID_ARG
     assert lib.mrnmf_select_extreme(h, 7, dummy, 8, dummy, None, 0, 3, dummy, None, None) == mrnmf.ERR_INVALID_ARG
