@@ -623,65 +623,100 @@ def run_ours(args):
     dev = Xd.device
     h = mrnmf.Handle()
     stream = torch.cuda.current_stream()
-    R = torch.empty((n, n), dtype=torch.float64, device=dev)
-    cs = torch.empty(n, dtype=torch.float64, device=dev)
-    GX = torch.empty((k, n), dtype=torch.float64, device=dev)
-    Ks = {mth: (torch.empty(r, dtype=torch.int32, device=dev), torch.empty(r, dtype=torch.float64, device=dev))
-          for mth in ("spa", "xray", "gp")}
-    Hs = {mth: torch.empty((r, n), dtype=torch.float64, device=dev) for mth in Ks}
-    outs = {mth: torch.empty(2, dtype=torch.float64, device=dev) for mth in Ks}
+    # Two sets of step outputs (R, column sums, GX, and each selection's K, H
+    # and residual): step i writes set i mod 2.
+    sets = []
+    for _ in range(2):
+        Ks = {mth: (torch.empty(r, dtype=torch.int32, device=dev), torch.empty(r, dtype=torch.float64, device=dev))
+              for mth in ("spa", "xray", "gp")}
+        sets.append({"R": torch.empty((n, n), dtype=torch.float64, device=dev),
+                     "cs": torch.empty(n, dtype=torch.float64, device=dev),
+                     "GX": torch.empty((k, n), dtype=torch.float64, device=dev), "Ks": Ks,
+                     "Hs": {mth: torch.empty((r, n), dtype=torch.float64, device=dev) for mth in Ks},
+                     "outs": {mth: torch.empty(2, dtype=torch.float64, device=dev) for mth in Ks}})
 
     # The three selections (and their NNLS and residual) depend only on R,
     # the column sums and GX: each runs on its own CUDA stream with its own
     # handle (a handle's small-step workspace serves one stream at a time),
-    # forked after the pass and joined before the step ends.
-    side = {mth: (torch.cuda.Stream(device=dev), mrnmf.Handle()) for mth in Ks}
-    ev_pass = torch.cuda.Event()
-    ev_side = {mth: torch.cuda.Event() for mth in Ks}
+    # forked from the stream `on` and joined back to it.
+    side = {mth: (torch.cuda.Stream(device=dev), mrnmf.Handle()) for mth in ("spa", "xray", "gp")}
+    ev_fork = torch.cuda.Event()
+    ev_side = {mth: torch.cuda.Event() for mth in side}
 
-    def selections(main):
-        ev_pass.record(main)
+    def selections(on, b):
+        st = sets[b]
+        ev_fork.record(on)
         for mth in ("xray", "spa", "gp"):
             s, hm = side[mth]
-            s.wait_event(ev_pass)
-            hm.select_extreme(mth, R=R, colsum=cs, GX=GX if mth == "gp" else None, r=r, out=Ks[mth], stream=s)
-            hm.nnls_h(R, Ks[mth][0], out=Hs[mth], stream=s)
-            hm.residual(R, Ks[mth][0], Hs[mth], out=outs[mth], stream=s)
+            s.wait_event(ev_fork)
+            hm.select_extreme(mth, R=st["R"], colsum=st["cs"], GX=st["GX"] if mth == "gp" else None, r=r,
+                              out=st["Ks"][mth], stream=s)
+            hm.nnls_h(st["R"], st["Ks"][mth][0], out=st["Hs"][mth], stream=s)
+            hm.residual(st["R"], st["Ks"][mth][0], st["Hs"][mth], out=st["outs"][mth], stream=s)
             ev_side[mth].record(s)
         for mth in ("xray", "spa", "gp"):
-            main.wait_event(ev_side[mth])
+            on.wait_event(ev_side[mth])
 
-    graph = None
+    # Overlap (default): the selections of step i run on their own stream
+    # while the pass of step i+1 runs; the pass of step i+2, which rewrites
+    # set i mod 2, waits for them.  Every step still does all of its work.
+    chain = torch.cuda.Stream(device=dev)
+    ev_pass = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_chain = [torch.cuda.Event(), torch.cuda.Event()]
+    graphs = [None, None]
     graph_launches = 0
+    mode = {"overlap": not args.no_overlap}
+    counter = [0]
 
     def step():
+        b = counter[0] & 1
+        counter[0] += 1
+        st = sets[b]
+        if mode["overlap"]:
+            stream.wait_event(ev_chain[b])  # the selections of step i-2 read this set
         # the pass runs eagerly (its leaf kernel is timed by events around it);
         # the selection chains replay as one CUDA graph once captured
-        h.tsqr_gp(Xd, k, w.seed, prec=args.prec, out=(R, cs, GX))
-        if graph is not None:
-            graph.replay()
+        h.tsqr_gp(Xd, k, w.seed, prec=args.prec, out=(st["R"], st["cs"], st["GX"]))
+        on = stream
+        if mode["overlap"]:
+            ev_pass[b].record(stream)
+            chain.wait_event(ev_pass[b])
+            on = chain
+        if graphs[b] is not None:
+            with torch.cuda.stream(on):
+                graphs[b].replay()
         else:
-            selections(stream)
+            selections(on, b)
+        if mode["overlap"]:
+            ev_chain[b].record(chain)
 
-    for _ in range(args.warmup):
+    def drain():
+        stream.wait_stream(chain)
+
+    for _ in range(max(args.warmup, 2)):
         step()
+    drain()
     h.sync()
     for _, hm in side.values():
         hm.sync()
     if not args.eager:
         # every buffer and workspace is in place after the warm-up, so the
-        # chains capture without allocations; the graph reads the current R,
-        # column sums and GX on every replay
-        cap = torch.cuda.Stream(device=dev)
-        cap.wait_stream(stream)
-        graph = torch.cuda.CUDAGraph()
-        l0 = mrnmf.kernel_launches()
-        with torch.cuda.graph(graph, stream=cap):
-            selections(cap)
-        graph_launches = mrnmf.kernel_launches() - l0
-        stream.wait_stream(cap)
+        # chains capture without allocations; graph b reads set b's R, column
+        # sums and GX on every replay
+        for b in range(2):
+            cap = torch.cuda.Stream(device=dev)
+            cap.wait_stream(stream)
+            g = torch.cuda.CUDAGraph()
+            l0 = mrnmf.kernel_launches()
+            with torch.cuda.graph(g, stream=cap):
+                selections(cap, b)
+            graph_launches = mrnmf.kernel_launches() - l0
+            stream.wait_stream(cap)
+            graphs[b] = g
         torch.cuda.synchronize()
-        step()
+        for _ in range(2):
+            step()
+        drain()
         h.sync()
         for _, hm in side.values():
             hm.sync()
@@ -703,6 +738,8 @@ def run_ours(args):
     for i in range(args.steps):
         h.profile_events(*leaf_ev[i])
         step()
+        if i + 1 == args.steps:
+            drain()  # the last step's selections end inside the timed region
         step_ev[i + 1].record(stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
@@ -714,7 +751,24 @@ def run_ours(args):
     h.sync()
     for _, hm in side.values():
         hm.sync()
+    last = sets[(counter[0] - 1) & 1]
+    R, Ks = last["R"], last["Ks"]
     t_dev = step_ev[0].elapsed_time(step_ev[-1]) / 1e3  # seconds
+    # the same steps without the overlap, for the record
+    seq_ms = None
+    if mode["overlap"]:
+        mode["overlap"] = False
+        nseq = max(3, min(args.steps, 20))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(nseq):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms = e0.elapsed_time(e1) / nseq
+        h.sync()
+        mode["overlap"] = True
     leaf_ms = [a.elapsed_time(b) for a, b in leaf_ev]
     t_max = time_over_ranks(t_dev, world, dev)
 
@@ -867,12 +921,14 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": w.name, "m": m, "n": n, "r": r, "k": k, "prec": args.prec,
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "selections": "eager, three streams" if graph is None else "CUDA graph, three streams",
+                           "selections": ("eager" if graphs[0] is None else "CUDA graph") + ", three streams, "
+                           + ("overlapping the next step's pass (double-buffered outputs)" if not args.no_overlap
+                              else "after the pass"),
                            "l2": f"input ({bytes_step / 1e9:.2f} GB) larger than L2 (129 MB); no flush needed",
                            "tune_file": os.path.relpath(os.environ["MRNMF_TUNE_FILE"], ROOT)
                            if os.environ.get("MRNMF_TUNE_FILE") else None},
                 "roofline": roofline, "roofline_other": roof_alu if roofline is roof_hbm else roof_hbm,
-                "leaf_ms": statistics.mean(leaf_ms), "r_error": r_err,
+                "leaf_ms": statistics.mean(leaf_ms), "sequential_ms_per_step": seq_ms, "r_error": r_err,
                 "K_spa": K_spa, "K_planted": P.K.tolist(), "forms": forms,
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "cpu_baseline": cpu,
                 "wall_s_timed": t_wall, "other_configs": other}
@@ -910,6 +966,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--eager", action="store_true", help="launch the selection chains eagerly (no CUDA graph)")
+    ap.add_argument("--no-overlap", action="store_true",
+                    help="run each step's selections after its pass, before the next pass starts")
     ap.add_argument("--cpu-rows", type=int, default=1_000_000)
     ap.add_argument("--cpu-rows-per-core", type=int, default=500_000,
                     help="rows per process of the all-cores oracle baseline")
