@@ -481,25 +481,24 @@ __device__ __forceinline__ void warp_stream_body(const LeafArgs& a, const int ct
                 gbuf[(4 * q + 3) * L + l] = g.w;
             }
             __syncwarp();
+            // packed FMAs: .x sums the even rows, .y the odd ones (the same
+            // two binary32 chains as one FMA a row would give)
             for (int q = 0; q < k; ++q) {
                 const float4* gq = reinterpret_cast<const float4*>(gbuf + q * L);
-                float s0 = 0.f, s1 = 0.f, u0 = 0.f, u1 = 0.f;
+                float2 p0 = make_float2(0.f, 0.f), p1 = p0;
 #pragma unroll
                 for (int l4 = 0; l4 < L / 4; ++l4) {
                     const float4 g = gq[l4];
-                    s0 = fmaf(g.x, a0[4 * l4], s0);
-                    u0 = fmaf(g.y, a0[4 * l4 + 1], u0);
-                    s0 = fmaf(g.z, a0[4 * l4 + 2], s0);
-                    u0 = fmaf(g.w, a0[4 * l4 + 3], u0);
+                    const float2 g01 = make_float2(g.x, g.y), g23 = make_float2(g.z, g.w);
+                    p0 = __ffma2_rn(g01, make_float2(a0[4 * l4], a0[4 * l4 + 1]), p0);
+                    p0 = __ffma2_rn(g23, make_float2(a0[4 * l4 + 2], a0[4 * l4 + 3]), p0);
                     if (NC == 2) {
-                        s1 = fmaf(g.x, a1[4 * l4], s1);
-                        u1 = fmaf(g.y, a1[4 * l4 + 1], u1);
-                        s1 = fmaf(g.z, a1[4 * l4 + 2], s1);
-                        u1 = fmaf(g.w, a1[4 * l4 + 3], u1);
+                        p1 = __ffma2_rn(g01, make_float2(a1[4 * l4], a1[4 * l4 + 1]), p1);
+                        p1 = __ffma2_rn(g23, make_float2(a1[4 * l4 + 2], a1[4 * l4 + 3]), p1);
                     }
                 }
-                if (own0) gxs[q * n + c0] += s0 + u0;
-                if (NC == 2 && own1) gxs[q * n + c1] += s1 + u1;
+                if (own0) gxs[q * n + c0] += p0.x + p0.y;
+                if (NC == 2 && own1) gxs[q * n + c1] += p1.x + p1.y;
             }
         }
 
