@@ -397,7 +397,7 @@ def run_stream(args, quiet=False):
 
 
 def tc_form_available(n: int, k: int) -> bool:
-    """The tensor-core (TF32x3) pass exists for this shape (the library's rule)."""
+    """The tensor-core pass (TF32X3 or TF32) exists for this shape (the library's rule)."""
     return 16 < n <= 256 and k <= (32 if n <= 64 else 48)
 
 
@@ -438,8 +438,8 @@ def run_illcond_forms(args, quiet=False):
     l1.record()
     forms = {}
     nbytes = 4.0 * m * n
-    for form in ("fp32", "tf32x3"):
-        if form == "tf32x3" and not tc_form_available(n, k):
+    for form in ("fp32", "tf32x3", "tf32"):
+        if form != "fp32" and not tc_form_available(n, k):
             continue
         h.tsqr_gp(Xd, k, w.seed, prec=form, out=(R, cs, GX))  # warm-up
         h.sync()
@@ -465,6 +465,8 @@ def run_illcond_forms(args, quiet=False):
     line = {"mode": "illcond", "workload": w.name, "m": m, "n": n, "k": k, "forms": forms}
     if "tf32x3" in forms:
         line["mixed_over_fp32"] = forms["fp32"]["pass_ms"] / forms["tf32x3"]["pass_ms"]
+    if "tf32" in forms:
+        line["tf32_over_fp32"] = forms["fp32"]["pass_ms"] / forms["tf32"]["pass_ms"]
     if not quiet:
         print(json.dumps(line), flush=True)
     return line
@@ -837,8 +839,8 @@ def run_ours(args):
     # ---- the pass alone in each arithmetic form available for this n (the
     # metric's "mixed vs FP32 at stated R error"), same resident X
     forms = {}
-    for form in ("fp32", "tf32x3"):
-        if form == "tf32x3" and not tc_form_available(n, k):
+    for form in ("fp32", "tf32x3", "tf32"):
+        if form != "fp32" and not tc_form_available(n, k):
             continue
         Rf = torch.empty((n, n), dtype=torch.float64, device=dev)
         csf = torch.empty(n, dtype=torch.float64, device=dev)
@@ -957,7 +959,7 @@ def main():
                          "batched: 256 independent problems; stream: 1.6e9 x 25 in 64M-row chunks; "
                          "illcond: the 1e8 x 200 workload in each arithmetic form")
     ap.add_argument("--batch", type=int, default=256)
-    ap.add_argument("--prec", choices=["auto", "fp32", "tf32x3"], default="auto")
+    ap.add_argument("--prec", choices=["auto", "fp32", "tf32x3", "tf32"], default="auto")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--rows", type=int, default=None, help="first ROWS rows only (profiling a smaller case)")
     ap.add_argument("--cols", type=int, default=8, help="columns of X in --mode pass")

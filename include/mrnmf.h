@@ -62,15 +62,18 @@ typedef enum { MRNMF_F32 = 0, MRNMF_F64 = 1 } mrnmf_dtype;
  * (hi*hi + hi*lo + lo*hi, the main term and the corrections accumulated
  * apart in FP32); R within 1e-5 of the FP64 oracle, slower than FP32 on
  * GB300, so AUTO does not pick it.  AUTO picks FP64 for F64 input, otherwise
- * FP32.  BF16 is a form of the projection alone (mrnmf_gauss_project_tc):
- * G and X rounded to bfloat16, exact products, FP32 accumulation; the passes
- * that form R reject it. */
+ * FP32.  TF32: the same tensor-core leaf with one TF32 product (hi*hi) in
+ * place of three; its error is that of 10-bit mantissas, well above the FP32
+ * form's (the tests state its bound).  BF16 is a form of the projection alone
+ * (mrnmf_gauss_project_tc): G and X rounded to bfloat16, exact products, FP32
+ * accumulation; the passes that form R reject it. */
 typedef enum {
     MRNMF_PREC_AUTO = 0,
     MRNMF_PREC_FP64 = 1,
     MRNMF_PREC_FP32 = 2,
     MRNMF_PREC_TF32X3 = 3,
-    MRNMF_PREC_BF16 = 4
+    MRNMF_PREC_BF16 = 4,
+    MRNMF_PREC_TF32 = 5
 } mrnmf_prec;
 
 typedef enum { MRNMF_SPA = 0, MRNMF_XRAY = 1, MRNMF_GP = 2 } mrnmf_method;

@@ -89,7 +89,8 @@ mrnmf_status check_pass_args(mrnmf_handle* h, const void* X, int64_t m, int32_t 
     if (m < n) return fail(h, MRNMF_ERR_INVALID_ARG, "need m >= n (tall-and-skinny X)");
     if (ldx < n) return fail(h, MRNMF_ERR_INVALID_ARG, "ldx < n");
     if (dtype != MRNMF_F32 && dtype != MRNMF_F64) return fail(h, MRNMF_ERR_INVALID_ARG, "dtype must be F32 or F64");
-    if (prec < MRNMF_PREC_AUTO || prec > MRNMF_PREC_TF32X3) return fail(h, MRNMF_ERR_INVALID_ARG, "bad prec");
+    if (prec < MRNMF_PREC_AUTO || prec > MRNMF_PREC_TF32 || prec == MRNMF_PREC_BF16)
+        return fail(h, MRNMF_ERR_INVALID_ARG, "bad prec");
     if (k < 0 || k > MRNMF_KMAX) return fail(h, MRNMF_ERR_INVALID_ARG, "k must be in [0, 64]");
     return MRNMF_OK;
 }
@@ -100,13 +101,13 @@ mrnmf_status setup_pass(mrnmf_handle* h, int n, int dtype, int prec, int k, uint
     prec = resolve_prec(prec, dtype, n, k);
     if (prec == MRNMF_PREC_FP32 && dtype == MRNMF_F64)
         return fail(h, MRNMF_ERR_INVALID_ARG, "FP32 pass needs F32 input (the library never narrows X)");
-    if (prec == MRNMF_PREC_TF32X3 && (dtype != MRNMF_F32 || !mrnmf::tc_supported(n, k)))
-        return fail(h, MRNMF_ERR_INVALID_ARG, "TF32X3 pass needs F32 input and a supported n");
+    if ((prec == MRNMF_PREC_TF32X3 || prec == MRNMF_PREC_TF32) && (dtype != MRNMF_F32 || !mrnmf::tc_supported(n, k)))
+        return fail(h, MRNMF_ERR_INVALID_ARG, "TF32X3 / TF32 pass needs F32 input and a supported n");
     mrnmf::PassState st;
     st.n = n;
     st.k = k;
     st.fp64 = prec == MRNMF_PREC_FP64;
-    st.tc = prec == MRNMF_PREC_TF32X3;
+    st.tc = prec == MRNMF_PREC_TF32X3 ? 1 : (prec == MRNMF_PREC_TF32 ? 2 : 0);
     st.tree64 = !st.fp64 && mrnmf::tree64_requested() && mrnmf::tree64_supported(n);
     st.seed = seed;
     st.rows_seen = 0;
@@ -356,7 +357,8 @@ mrnmf_status mrnmf_stream_begin(mrnmf_handle* h, int32_t n, int32_t dtype, int32
     if (!h) return MRNMF_ERR_INVALID_ARG;
     if (n < 1 || n > MRNMF_NMAX) return fail(h, MRNMF_ERR_INVALID_ARG, "n must be in [1, 256]");
     if (dtype != MRNMF_F32 && dtype != MRNMF_F64) return fail(h, MRNMF_ERR_INVALID_ARG, "bad dtype");
-    if (prec < MRNMF_PREC_AUTO || prec > MRNMF_PREC_TF32X3) return fail(h, MRNMF_ERR_INVALID_ARG, "bad prec");
+    if (prec < MRNMF_PREC_AUTO || prec > MRNMF_PREC_TF32 || prec == MRNMF_PREC_BF16)
+        return fail(h, MRNMF_ERR_INVALID_ARG, "bad prec");
     if (k < 0 || k > MRNMF_KMAX) return fail(h, MRNMF_ERR_INVALID_ARG, "k must be in [0, 64]");
     mrnmf_status s = bind_device(h);
     if (s != MRNMF_OK) return s;

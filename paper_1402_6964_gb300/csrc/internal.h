@@ -24,7 +24,7 @@ struct PassState {
     int tri = 0;        // triangle slots the leaf leaves for the tree (P, or P / 4 when
                         // the warp leaf folds each CTA's four streams into one)
     int fp64 = 0;       // 1: triangles and reflectors in binary64, else binary32
-    int tc = 0;         // 1: tensor-core (TF32x3) leaf
+    int tc = 0;         // tensor-core leaf: 1 = TF32X3 (three products), 2 = TF32 (one); 0 = none
     int tree64 = 0;     // 1: binary32 leaf triangles reduced by a binary64 tree
     int gp_form = 0;    // projection-only pass on tcgen05: MRNMF_PREC_TF32X3 or MRNMF_PREC_BF16
                         // (0: SIMT, or TF32X3 with MRNMF_GP_TC=1)

@@ -24,6 +24,7 @@ struct LeafArgs {
     int check;             // reject negative / NaN entries
     int* status;
     int tile_rows;         // warp leaf: tile height the pass was planned with (0 = warp_leaf_rows_per_tile)
+    int tc_split;          // tensor-core leaf: 1 = three TF32 products (hi*hi + hi*lo + lo*hi), 0 = one
 };
 
 // Batched pass: one problem per entry, CTAs described one by one.

@@ -499,6 +499,7 @@ cudaError_t pass_push(PassState& st, const void* X, int64_t rows, int64_t ldx, i
         e = launch_gp_tc(static_cast<const float*>(X), rows, ldx, st.n, st.k, st.rows_seen, st.seed, st.P, st.cs,
                          st.gx, status, gp_form == MRNMF_PREC_BF16, s);
     } else if (st.tc && !xf64 && qr) {
+        a.tc_split = st.tc == 1;
         const int L = tc_leaf_rows_per_tile();
         int64_t pw = (rows + st.P - 1) / st.P;
         a.rows_per_cta = ((pw + L - 1) / L) * L;

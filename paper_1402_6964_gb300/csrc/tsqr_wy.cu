@@ -1,6 +1,6 @@
 // tsqr_wy.cu -- the pass over X with the trailing updates of the leaf QR on
-// the tensor cores: tcgen05 MMAs in three-pass TF32 with FP32 accumulation,
-// for 16 < n <= 256.
+// the tensor cores: tcgen05 MMAs in TF32 with FP32 accumulation, three
+// products per product of values (TF32X3) or one (TF32), for 16 < n <= 256.
 //
 // One CTA of 128 threads per row stream.  Each 128-row tile A of X is folded
 // into the stream's running triangle R (binary32; it stays in the stream's
@@ -39,9 +39,11 @@
 // summed from the same chunks, pairwise in binary32 over 16 rows and in
 // binary64 across chunks.
 //
-// Precision: every product is formed as hi*hi + hi*lo + lo*hi with hi = the
-// value as the tensor core reads it (kind::tf32 keeps the top 19 bits of a
-// binary32 operand and drops the rest) and lo = x - hi, exact in binary32.
+// Precision: in the TF32X3 form every product is formed as hi*hi + hi*lo +
+// lo*hi with hi = the value as the tensor core reads it (kind::tf32 keeps the
+// top 19 bits of a binary32 operand and drops the rest) and lo = x - hi,
+// exact in binary32; the TF32 form (LeafArgs::tc_split = 0) takes hi*hi
+// alone, skipping the low parts and the correction MMAs.
 // The MMA instructions are issued by one elected lane of warp 0, unrolled,
 // with their operands in tensor memory wherever the operand spans the 128
 // lanes: on GB300 such MMAs cost a fraction of those that read a 128-row
@@ -154,6 +156,7 @@ __global__ void __launch_bounds__(kRows, NP <= 64 ? 2 : 1) tsqr_wy_kernel(const 
     const unsigned FULL = 0xffffffffu;
     const int n = a.n, nt = (n + 15) & ~15;
     const int k = (KP > 0 && a.gx) ? a.k : 0;
+    const bool split = a.tc_split != 0;  // three products (TF32X3), or one (TF32)
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int cta = blockIdx.x;
     float* XS = reinterpret_cast<float*>(sm + M::oXS);
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(kRows, NP <= 64 ? 2 : 1) tsqr_wy_kernel(const 
                         const float v = q < k ? gv[i] : 0.f;
                         const uint32_t off = sw128_off(q, t, KP / 8);
                         *reinterpret_cast<float*>(sm + M::oGsH + off) = v;
-                        *reinterpret_cast<float*>(sm + M::oGsL + off) = tc::tf32_lo(v);
+                        if (split) *reinterpret_cast<float*>(sm + M::oGsL + off) = tc::tf32_lo(v);
                     }
                 }
                 tc::fence_async_smem();
@@ -369,8 +372,9 @@ __global__ void __launch_bounds__(kRows, NP <= 64 ? 2 : 1) tsqr_wy_kernel(const 
                         const uint32_t off = sw128_off(c, rb + 4 * i4, kNB / 8);
                         const float4 v = make_float4(av[4 * i4], av[4 * i4 + 1], av[4 * i4 + 2], av[4 * i4 + 3]);
                         *reinterpret_cast<float4*>(sm + M::oYsH + off) = v;
-                        *reinterpret_cast<float4*>(sm + M::oYsL + off) =
-                            make_float4(tc::tf32_lo(v.x), tc::tf32_lo(v.y), tc::tf32_lo(v.z), tc::tf32_lo(v.w));
+                        if (split)
+                            *reinterpret_cast<float4*>(sm + M::oYsL + off) =
+                                make_float4(tc::tf32_lo(v.x), tc::tf32_lo(v.y), tc::tf32_lo(v.z), tc::tf32_lo(v.w));
                     }
                     tc::fence_async_smem();
                 }
@@ -409,7 +413,7 @@ __global__ void __launch_bounds__(kRows, NP <= 64 ? 2 : 1) tsqr_wy_kernel(const 
                         lo[q] = tc::tf32_lo(y[q]);
                     }
                     tc::tmem_st16_nowait(tq + M::cYH, y);
-                    tc::tmem_st16_nowait(tq + M::cYL, lo);
+                    if (split) tc::tmem_st16_nowait(tq + M::cYL, lo);
                     tc::tmem_wait_st();
                 }
 
@@ -440,7 +444,7 @@ __global__ void __launch_bounds__(kRows, NP <= 64 ? 2 : 1) tsqr_wy_kernel(const 
                                 }
                                 if (p == 0 && c < n) cs_acc[lb] += (double)sum16(v);
                                 tc::tmem_st16_nowait(tq + M::cAT(buf, lb, 0), v);
-                                tc::tmem_st16_nowait(tq + M::cAT(buf, lb, 1), lo);
+                                if (split) tc::tmem_st16_nowait(tq + M::cAT(buf, lb, 1), lo);
                                 tc::tmem_wait_st();
                             }
                         }
@@ -464,16 +468,20 @@ __global__ void __launch_bounds__(kRows, NP <= 64 ? 2 : 1) tsqr_wy_kernel(const 
                                         // and the corrections are 2^-11 of the main term
                                         const uint32_t za = tmem + M::cZ(0, lb), zb = tmem + M::cZ(1, lb);
                                         tc::mma_tf32_ts(za, ah, bh, idZ, (q | ks) != 0);
-                                        tc::mma_tf32_ts(zb, ah, bl, idZ, (q | ks) != 0);
-                                        tc::mma_tf32_ts(zb, al, bh, idZ, true);
+                                        if (split) {
+                                            tc::mma_tf32_ts(zb, ah, bl, idZ, (q | ks) != 0);
+                                            tc::mma_tf32_ts(zb, al, bh, idZ, true);
+                                        }
                                         if (KP > 0 && gp) {
                                             const uint32_t idG = tc::instr_desc(2, 128, KP > 0 ? KP : 16);
                                             const uint64_t gh = sw128_step(sb + M::oGsH, k0, KP / 8);
                                             const uint64_t gl = sw128_step(sb + M::oGsL, k0, KP / 8);
                                             const uint32_t gxa = tmem + M::cGX(lb);
                                             tc::mma_tf32_ts(gxa, ah, gh, idG, !(gx_fresh && q == 0 && ks == 0));
-                                            tc::mma_tf32_ts(gxa, ah, gl, idG, true);
-                                            tc::mma_tf32_ts(gxa, al, gh, idG, true);
+                                            if (split) {
+                                                tc::mma_tf32_ts(gxa, ah, gl, idG, true);
+                                                tc::mma_tf32_ts(gxa, al, gh, idG, true);
+                                            }
                                         }
                                     }
                                 }
@@ -496,11 +504,14 @@ __global__ void __launch_bounds__(kRows, NP <= 64 ? 2 : 1) tsqr_wy_kernel(const 
                 for (int lb = 0; lb < LB; ++lb) {
                     const int cw = 128 * lb + 32 * warp;
                     if (cw < nt && cw + 32 > trail0) {
-                        float z[16], zb[16];
+                        float z[16];
                         tc::tmem_ld16(tq + M::cZ(0, lb), z);
-                        tc::tmem_ld16(tq + M::cZ(1, lb), zb);
+                        if (split) {  // the corrections' accumulator is written by the three-product form only
+                            float zb[16];
+                            tc::tmem_ld16(tq + M::cZ(1, lb), zb);
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) z[q] += zb[q];
+                            for (int q = 0; q < 16; ++q) z[q] += zb[q];
+                        }
                         const int c = 128 * lb + t;
                         if (c >= trail0 && c < nt) {
                             float w[16];
@@ -528,8 +539,9 @@ __global__ void __launch_bounds__(kRows, NP <= 64 ? 2 : 1) tsqr_wy_kernel(const 
                                     make_float4(-w[4 * q4], -w[4 * q4 + 1], -w[4 * q4 + 2], -w[4 * q4 + 3]);
                                 const uint32_t off = wq_off(nrow, 4 * q4);
                                 *reinterpret_cast<float4*>(sm + M::oWsH + off) = v;
-                                *reinterpret_cast<float4*>(sm + M::oWsL + off) = make_float4(
-                                    tc::tf32_lo(v.x), tc::tf32_lo(v.y), tc::tf32_lo(v.z), tc::tf32_lo(v.w));
+                                if (split)
+                                    *reinterpret_cast<float4*>(sm + M::oWsL + off) = make_float4(
+                                        tc::tf32_lo(v.x), tc::tf32_lo(v.y), tc::tf32_lo(v.z), tc::tf32_lo(v.w));
                             }
                         }
                     }
@@ -548,8 +560,10 @@ __global__ void __launch_bounds__(kRows, NP <= 64 ? 2 : 1) tsqr_wy_kernel(const 
                             const uint64_t wl = tc::smem_desc(sb + M::oWsL + 256u * ks, 128u, 512u);
                             const uint32_t yh = tmem + M::cYH + 8 * ks, yl = tmem + M::cYL + 8 * ks;
                             tc::mma_tf32_ts(d, yh, wh, idW, true);
-                            tc::mma_tf32_ts(d, yh, wl, idW, true);
-                            tc::mma_tf32_ts(d, yl, wh, idW, true);
+                            if (split) {
+                                tc::mma_tf32_ts(d, yh, wl, idW, true);
+                                tc::mma_tf32_ts(d, yl, wh, idW, true);
+                            }
                         }
                         tc::mma_commit(&bar[2]);
                     }

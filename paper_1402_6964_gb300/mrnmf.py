@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmrnmf.so")
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NO_MEMORY, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_BAD_INPUT, ERR_RANK_DEFICIENT = range(8)
 F32, F64 = 0, 1
-PREC = {"auto": 0, "fp64": 1, "fp32": 2, "tf32x3": 3, "bf16": 4}
+PREC = {"auto": 0, "fp64": 1, "fp32": 2, "tf32x3": 3, "bf16": 4, "tf32": 5}
 METHOD = {"spa": 0, "xray": 1, "gp": 2}
 
 EXPORTS = [

@@ -7,6 +7,18 @@ FP32 accumulation).  It is held to the same bounds as the binary32 pass:
   R      : ||R_gpu - R_orc||_F / ||R_orc||_F <= 1e-5
   colsum : relative 1e-6
   GX     : |GX_gpu - GX_orc| <= 2e-6 * (|G|^T |X|) elementwise
+
+The TF32 form (MRNMF_PREC_TF32) runs the same leaf with one TF32 product in
+place of three: its operands keep 10-bit mantissas, so it is held to its own
+stated bounds.  R's are about three times the largest error measured on
+GB300 (4.8e-4 to 6.3e-4 on uniform X, 1.4e-3 with 10^U(0,3) column scaling).
+GX's follows from the arithmetic: truncating each operand to TF32 moves it
+by less than 2^-10 of itself, so each product is within 2^-9 of the exact
+one, and the binary32 sums add the 2e-6 of the other forms:
+
+  R      : relative Frobenius 2e-3 (uniform X), 5e-3 (10^U(0,3) columns)
+  colsum : relative 1e-6 (summed from the same binary32 values)
+  GX     : (2^-9 + 2e-6) * (|G|^T |X|) elementwise
 """
 import numpy as np
 import pytest
@@ -17,6 +29,9 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 R_TOL = 1e-5
+R_TOL_TF32 = 2e-3
+R_TOL_TF32_SCALED = 5e-3
+GX_TOL_TF32 = 2.0 ** -9 + 2e-6
 
 
 @pytest.fixture(scope="module")
@@ -152,12 +167,42 @@ def test_tf32x3_bad_input_is_reported(h):
 def test_tf32x3_rejects_unsupported_shape(h):
     # the tensor-core form covers 16 < n <= 256, with k <= 32 for n <= 64 and k <= 48 above
     from paper_1402_6964_gb300 import mrnmf
-    X = synth.random_nonneg(1000, 10, seed=2)
-    with pytest.raises(mrnmf.MrnmfError) as e:
-        h.tsqr_r(dev(X), prec="tf32x3")
-    assert e.value.status == mrnmf.ERR_INVALID_ARG
-    for n, k in [(50, 33), (100, 49)]:
-        X = synth.random_nonneg(1000, n, seed=2)
+    for prec in ("tf32x3", "tf32"):
+        X = synth.random_nonneg(1000, 10, seed=2)
         with pytest.raises(mrnmf.MrnmfError) as e:
-            h.tsqr_gp(dev(X), k, seed=1, prec="tf32x3")
+            h.tsqr_r(dev(X), prec=prec)
         assert e.value.status == mrnmf.ERR_INVALID_ARG
+        for n, k in [(50, 33), (100, 49)]:
+            X = synth.random_nonneg(1000, n, seed=2)
+            with pytest.raises(mrnmf.MrnmfError) as e:
+                h.tsqr_gp(dev(X), k, seed=1, prec=prec)
+            assert e.value.status == mrnmf.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("m,n,k", [(200_000, 50, 0), (200_000, 50, 20), (50_000, 20, 8), (60_000, 200, 40),
+                                   (40_000, 256, 0), (3001, 65, 17), (129, 24, 0)])
+def test_tsqr_tf32_single_product_within_its_bound(h, oracle, m, n, k):
+    X = synth.random_nonneg(m, n, seed=7 + n)
+    X64 = X.astype(np.float64)
+    if k:
+        R, cs, GX = h.tsqr_gp(dev(X), k, seed=3, prec="tf32")
+    else:
+        R, cs = h.tsqr_r(dev(X), prec="tf32")
+    h.sync()
+    Rg = host(R)
+    assert np.all(np.tril(Rg, -1) == 0) and np.all(np.diag(Rg) >= 0)
+    err = rel_fro(Rg, oracle.qr_r(X64))
+    assert err <= R_TOL_TF32, err
+    # the single product is a different form: its error is far from the three-product form's
+    assert err > 1e-5
+    np.testing.assert_allclose(host(cs), oracle.colsum(X64), rtol=1e-6)
+    if k:
+        GXo = oracle.gauss_project(X64, k, 3)
+        assert np.all(np.abs(host(GX) - GXo) <= GX_TOL_TF32 * gx_bound(X, k, 3) + 1e-12)
+
+
+def test_tsqr_tf32_scaled_columns(h, oracle):
+    X, _ = synth.planted_separable(100_000, 100, 10, seed=107, noise=1e-3, decades=3.0)
+    R, _ = h.tsqr_r(dev(X), prec="tf32")
+    h.sync()
+    assert rel_fro(host(R), oracle.qr_r(X.astype(np.float64))) <= R_TOL_TF32_SCALED
