@@ -145,3 +145,45 @@ def test_tf32x3_projection_by_name_matches_oracle():
         assert np.all(np.abs(GX.cpu().numpy() - orc.gauss_project(X64, k, 77, row0=5)) <= bound), (m, n, k)
         np.testing.assert_allclose(cs.cpu().numpy(), orc.colsum(X64), rtol=1e-6)
     h.close()
+
+
+def _agree_under_margin(Kg, Ko, gap, margin, n):
+    """Picks agree at every step whose oracle gap exceeds `margin`; from the
+    first divergence at a smaller gap on, only validity is checked (distinct
+    indices in [0, n))."""
+    Kg = [int(v) for v in Kg]
+    assert len(set(Kg)) == len(Kg) and all(0 <= v < n for v in Kg), Kg
+    for t in range(len(Ko)):
+        if Kg[t] != Ko[t]:
+            assert gap[t] < margin, (t, Kg[t], Ko[t], gap[t], margin)
+            return t
+    return len(Ko)
+
+
+def test_gp_selection_on_bf16_projection_matches_oracle():
+    """GP selection (Sec. 2.3) on the BF16 projection: K against the oracle's GP
+    run on the bfloat16-rounded G and X with binary64 sums, and against the
+    oracle's GP on the unrounded inputs, each under the margin rule (100 times
+    the relative error of that comparison's GX); both recover the planted
+    columns of the near-separable input."""
+    import oracle as orc
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_6964_gb300 import build, mrnmf, synth
+    build.build()
+    m, n, r, k, seed = 200_000, 50, 10, 20, 7
+    X, P = synth.planted_separable(m, n, r, seed=1402002, noise=1e-3)
+    X64 = X.astype(np.float64)
+    h = mrnmf.Handle()
+    GX, cs = h.gauss_project_tc(torch.from_numpy(X).cuda(), k, seed=seed, form="bf16")
+    K, gap = h.select_extreme("gp", colsum=cs, GX=GX, r=r)
+    h.sync()
+    h.close()
+    got, Kg = GX.cpu().numpy(), K.cpu().numpy()
+    G = orc.gauss_matrix(seed, 0, m, k)
+    so = orc.colsum(X64)
+    for ref in (_bf16(G).astype(np.float64).T @ _bf16(X).astype(np.float64), G.T @ X64):
+        Ko, _, go = orc.gp_select(ref, so, r)
+        margin = max(100.0 * float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))), 1e-12)
+        _agree_under_margin(Kg, Ko, go, margin, n)
+    assert sorted(int(v) for v in Kg) == list(P.K)
