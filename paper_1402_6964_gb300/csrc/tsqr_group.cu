@@ -46,14 +46,29 @@ __host__ __device__ constexpr int group_lanes(int n) { return n <= 4 ? 4 : n <= 
 
 __host__ __device__ inline size_t gup(size_t b, size_t a) { return (b + a - 1) / a * a; }
 
+// Partial dot products of the 16-lane groups (n > 8), transposed: group g,
+// column c, lane s at g * kPG + c * kPC + s.  The strides keep both the
+// stores (a column's 16 lanes, two groups 16 banks apart) and lane c's four
+// 16-byte loads on distinct banks.
+constexpr int kPC = 20;            // floats per column
+constexpr int kPG = 16 * kPC + 16;  // floats per group
+
 // Per-warp shared memory: [mbarrier | super-tile (32 * 64/S) x n | fold pivots
-// 2 x (32/S) x (kLF + 4)].  After the tile loop the super-tile area holds the
-// groups' triangles for the fold ((32/S) n^2 <= 32 (64/S) n floats).
+// 2 x (32/S) x (kLF + 4) | partial dots 2 x kPG (n > 8)].  After the tile
+// loop the super-tile area holds the groups' triangles for the fold
+// ((32/S) n^2 <= 32 (64/S) n floats).
+template <int NC>
+__host__ __device__ constexpr bool group_smem_sums() { return group_lanes(NC) == 16; }
+
+template <int NC>
+__host__ __device__ inline size_t group_pub_floats() { return 2 * (32 / group_lanes(NC)) * (kLF + 4); }
+
 template <int NC>
 __host__ __device__ inline size_t group_slice_bytes()
 {
-    constexpr int S = group_lanes(NC), NG = 32 / S, TR = 32 * (64 / S);
-    return gup(128 + gup(sizeof(float) * (size_t)TR * NC, 128) + sizeof(float) * 2 * NG * (kLF + 4), 128);
+    constexpr int S = group_lanes(NC), TR = 32 * (64 / S);
+    const size_t red = group_smem_sums<NC>() ? sizeof(float) * 2 * kPG : 0;
+    return gup(128 + gup(sizeof(float) * (size_t)TR * NC, 128) + sizeof(float) * group_pub_floats<NC>() + red, 128);
 }
 
 // Fold steps, column layout: lane s of group g holds column s of a kLF-row
@@ -111,31 +126,55 @@ __device__ __forceinline__ void fold_steps(float (&a)[kLF], float (&r)[NC], floa
 // group's lanes, and lane c's update factor w'_c / (d beta) is broadcast.
 // J is a template parameter so that every register index is static.
 template <int NC, int J>
-__device__ __forceinline__ void row_step(float2 (&A2)[64 / group_lanes(NC) / 2][NC], float (&r)[NC], int s, int g)
+__device__ __forceinline__ void row_step(float2 (&A2)[64 / group_lanes(NC) / 2][NC], float (&r)[NC], int s, int g,
+                                         float* red)
 {
     constexpr int S = group_lanes(NC), RP = 64 / S / 2;
     const unsigned FULL = 0xffffffffu;
     const int lead = g * S;
     const bool own = s < NC;
-    float gv[NC];
+    float sig, gs = 0.f;
+    if constexpr (group_smem_sums<NC>()) {
+        // 16-lane groups: the partials go to shared memory transposed, and lane c
+        // sums the 16 of its own column (one fixed tree), so g_c arrives where it
+        // is used; sigma = g_J is broadcast from lane J
+        float* pg = red + g * kPG;
 #pragma unroll
-    for (int c = J; c < NC; ++c) {
-        float2 acc = __fmul2_rn(A2[0][J], A2[0][c]);
+        for (int c = J; c < NC; ++c) {
+            float2 acc = __fmul2_rn(A2[0][J], A2[0][c]);
 #pragma unroll
-        for (int p = 1; p < RP; ++p) acc = __ffma2_rn(A2[p][J], A2[p][c], acc);
-        gv[c] = acc.x + acc.y;
+            for (int p = 1; p < RP; ++p) acc = __ffma2_rn(A2[p][J], A2[p][c], acc);
+            pg[c * kPC + s] = acc.x + acc.y;
+        }
+        __syncwarp();
+        if (s >= J && s < NC) {
+            const float4* q = reinterpret_cast<const float4*>(pg + s * kPC);
+            const float4 u0 = q[0], u1 = q[1], u2 = q[2], u3 = q[3];
+            gs = (((u0.x + u0.y) + (u0.z + u0.w)) + ((u1.x + u1.y) + (u1.z + u1.w))) +
+                 (((u2.x + u2.y) + (u2.z + u2.w)) + ((u3.x + u3.y) + (u3.z + u3.w)));
+        }
+        __syncwarp();  // every read of this step's partials is done before the next step writes
+        sig = __shfl_sync(FULL, gs, lead + J);
+    } else {
+        float gv[NC];
+#pragma unroll
+        for (int c = J; c < NC; ++c) {
+            float2 acc = __fmul2_rn(A2[0][J], A2[0][c]);
+#pragma unroll
+            for (int p = 1; p < RP; ++p) acc = __ffma2_rn(A2[p][J], A2[p][c], acc);
+            gv[c] = acc.x + acc.y;
+        }
+        // group sums (a butterfly: every lane adds the same operands in the same tree)
+#pragma unroll
+        for (int o = 1; o < S; o <<= 1) {
+#pragma unroll
+            for (int c = J; c < NC; ++c) gv[c] += __shfl_xor_sync(FULL, gv[c], o);
+        }
+        sig = gv[J];
+#pragma unroll
+        for (int c = J + 1; c < NC; ++c) gs = (s == c) ? gv[c] : gs;
     }
-    // group sums (a butterfly: every lane adds the same operands in the same tree)
-#pragma unroll
-    for (int o = 1; o < S; o <<= 1) {
-#pragma unroll
-        for (int c = J; c < NC; ++c) gv[c] += __shfl_xor_sync(FULL, gv[c], o);
-    }
-    const float sig = gv[J];
     const float alpha = __shfl_sync(FULL, r[J], lead + J);
-    float gs = 0.f;
-#pragma unroll
-    for (int c = J + 1; c < NC; ++c) gs = (s == c) ? gv[c] : gs;
     float fs = 0.f;
     if (sig > 0.f) {
         const HhScalars hs = hh_scalars(alpha, sig);
@@ -158,16 +197,17 @@ __device__ __forceinline__ void row_step(float2 (&A2)[64 / group_lanes(NC) / 2][
 
 template <int NC, int... J>
 __device__ __forceinline__ void row_steps_seq(float2 (&A2)[64 / group_lanes(NC) / 2][NC], float (&r)[NC], int s, int g,
-                                              std::integer_sequence<int, J...>)
+                                              float* red, std::integer_sequence<int, J...>)
 {
-    (row_step<NC, J>(A2, r, s, g), ...);
+    (row_step<NC, J>(A2, r, s, g, red), ...);
 }
 
 // Column steps 0 .. NC-1 of one block.
 template <int NC>
-__device__ __forceinline__ void row_steps(float2 (&A2)[64 / group_lanes(NC) / 2][NC], float (&r)[NC], int s, int g)
+__device__ __forceinline__ void row_steps(float2 (&A2)[64 / group_lanes(NC) / 2][NC], float (&r)[NC], int s, int g,
+                                          float* red)
 {
-    row_steps_seq<NC>(A2, r, s, g, std::make_integer_sequence<int, NC>{});
+    row_steps_seq<NC>(A2, r, s, g, red, std::make_integer_sequence<int, NC>{});
 }
 
 template <int NC>
@@ -195,6 +235,7 @@ __global__ void __launch_bounds__(kGW * 32, 4) tsqr_group_kernel(const LeafArgs 
     uint64_t* bar = reinterpret_cast<uint64_t*>(base);
     float* tile = reinterpret_cast<float*>(base + 128);
     float* pub = tile + gup((size_t)TR * NC, 32);
+    float* red = pub + group_pub_floats<NC>();  // partial dots (16-lane groups)
     if (lane == 0) tc::mbar_init(bar, 1);
     __syncwarp();
 
@@ -331,7 +372,7 @@ __global__ void __launch_bounds__(kGW * 32, 4) tsqr_group_kernel(const LeafArgs 
             }
         }
 
-        row_steps<NC>(A2, r, s, g);
+        row_steps<NC>(A2, r, s, g, red);
 
         if ((t + 1) % kGFlush == 0 || t + 1 == ntiles) {
             float mine = 0.f;
