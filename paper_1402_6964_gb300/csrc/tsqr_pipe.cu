@@ -35,7 +35,7 @@ namespace {
 
 constexpr int kL = 32;          // tile height
 constexpr int kD = 2;           // ring slots (tiles in flight)
-constexpr int kRS = kL + 4;     // ring entry: L values, then d, 1/beta, 1/d, pad
+constexpr int kRS = kL + 4;     // ring entry: L values, then d, 1/beta, 1/d, v_j' v_(j+1)
 constexpr int kMaxW = 8;        // warps (n <= 256)
 constexpr int kFlushT = 32;     // tiles between binary64 flushes
 
@@ -283,7 +283,55 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
             if (!ok) break;
             if (GP && b == 0) project(gs);
             const int j1 = bstart(b + 1);
-            for (int j = bstart(b); j < j1; ++j) {
+            int j = bstart(b);
+            // two reflectors per dependent chain: both dot products from the same
+            // column, the second corrected by the pair coefficient
+            // c = v_j' v_(j+1) that the producer published (g_(j+1) of the column
+            // after reflector j is g_(j+1) + f_j c); the update is the same two
+            // FMAs per element as applying them one after the other
+            for (; j + 1 < j1; j += 2) {
+                const float* rv0 = rs + (size_t)j * kRS;
+                const float* rv1 = rv0 + kRS;
+                const float4* p0 = reinterpret_cast<const float4*>(rv0);
+                const float4* p1 = reinterpret_cast<const float4*>(rv1);
+                float ga = 0.f, gb = 0.f, gc = 0.f, gd = 0.f, ha = 0.f, hb = 0.f, hc = 0.f, hd = 0.f;
+#pragma unroll
+                for (int l4 = 0; l4 < kL / 4; ++l4) {
+                    const float4 v = p0[l4], u = p1[l4];
+                    ga = fmaf(v.x, av[4 * l4], ga);
+                    gb = fmaf(v.y, av[4 * l4 + 1], gb);
+                    gc = fmaf(v.z, av[4 * l4 + 2], gc);
+                    gd = fmaf(v.w, av[4 * l4 + 3], gd);
+                    ha = fmaf(u.x, av[4 * l4], ha);
+                    hb = fmaf(u.y, av[4 * l4 + 1], hb);
+                    hc = fmaf(u.z, av[4 * l4 + 2], hc);
+                    hd = fmaf(u.w, av[4 * l4 + 3], hd);
+                }
+                const float g0 = (ga + gb) + (gc + gd);
+                float g1 = (ha + hb) + (hc + hd);
+                const float d0 = rv0[kL], rb0 = rv0[kL + 1], rd0 = rv0[kL + 2], c01 = rv0[kL + 3];
+                const float d1 = rv1[kL], rb1 = rv1[kL + 1], rd1 = rv1[kL + 2];
+                if (own) {
+                    const int e0 = pk(j, n) + c, e1 = pk(j + 1, n) + c;
+                    const float r0 = Rs[e0], r1 = Rs[e1];
+                    const float wp0 = fmaf(d0, r0, g0);
+                    const float f0 = (wp0 * rd0) * rb0;
+                    Rs[e0] = fmaf(wp0, rb0, r0);
+                    g1 = fmaf(f0, c01, g1);
+                    const float wp1 = fmaf(d1, r1, g1);
+                    const float f1 = (wp1 * rd1) * rb1;
+                    Rs[e1] = fmaf(wp1, rb1, r1);
+#pragma unroll
+                    for (int l4 = 0; l4 < kL / 4; ++l4) {
+                        const float4 v = p0[l4], u = p1[l4];
+                        av[4 * l4] = fmaf(f1, u.x, fmaf(f0, v.x, av[4 * l4]));
+                        av[4 * l4 + 1] = fmaf(f1, u.y, fmaf(f0, v.y, av[4 * l4 + 1]));
+                        av[4 * l4 + 2] = fmaf(f1, u.z, fmaf(f0, v.z, av[4 * l4 + 2]));
+                        av[4 * l4 + 3] = fmaf(f1, u.w, fmaf(f0, v.w, av[4 * l4 + 3]));
+                    }
+                }
+            }
+            for (; j < j1; ++j) {
                 const float* rv = rs + (size_t)j * kRS;
                 const float4* p4 = reinterpret_cast<const float4*>(rv);
                 float ga = 0.f, gb = 0.f, gc = 0.f, gd = 0.f;
@@ -372,6 +420,10 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
                 rv[kL + 1] = rb;
                 rv[kL + 2] = rd;
             }
+            // the pair coefficient v_(j-1)' v_j for the consumers: lane j-1 still holds
+            // v_(j-1) (a reflector leaves its own column alone), so its dot product
+            // with this step's pivot is that coefficient
+            if (c == j - 1 && j > jb0) rs[(size_t)(j - 1) * kRS + kL + 3] = g;
             __syncwarp();
         }
         if (lane == 0 && w < W - 1) bar_arrive(&pub[s * kMaxW + w]);
