@@ -21,8 +21,8 @@
 //
 // Column sums and the Gaussian projection (Algorithm 1, Sec. 3.2) are folded
 // in: warp 0 draws each tile's G into the slot, every thread accumulates
-// G' A(:, c) for its column in binary32, flushed to binary64 every kFlush
-// tiles.
+// G' A(:, c) for its column in binary32 (in shared memory), flushed to
+// binary64 every kFlush tiles.
 #include <cstdlib>
 
 #include "common.cuh"
@@ -43,10 +43,12 @@ __host__ __device__ inline int pk(int j, int n) { return j * n - (j * (j + 1)) /
 __host__ __device__ inline size_t up16(size_t b) { return (b + 15) / 16 * 16; }
 
 struct PipeLayout {
-    size_t ring, gbuf, bars, flag, total;
+    size_t ring, gbuf, gx, bars, flag, total;
 };
 
-__host__ __device__ inline PipeLayout pipe_layout(int n, int k)
+// gxs: the projection's binary32 partials in shared memory ([coordinate][column])
+// instead of registers
+__host__ __device__ inline PipeLayout pipe_layout(int n, int k, bool gxs = false)
 {
     const int kp = (k + 3) & ~3;
     PipeLayout p;
@@ -55,6 +57,8 @@ __host__ __device__ inline PipeLayout pipe_layout(int n, int k)
     off += up16(sizeof(float) * (size_t)kD * n * kRS);
     p.gbuf = off;
     off += up16(sizeof(float) * (size_t)kD * kp * kL);
+    p.gx = off;
+    if (gxs) off += up16(sizeof(float) * (size_t)k * n);
     p.bars = off;
     off += sizeof(uint64_t) * 2 * kD * kMaxW;
     p.flag = off;
@@ -158,7 +162,9 @@ __global__ void __launch_bounds__(128) wait_selftest_kernel(int missing, uint64_
 // block may have more warps than the problem's column blocks (batched
 // launches size the block for the widest problem): those warps only meet the
 // CTA-wide barriers.
-template <int KMAX>
+// GXS: the projection's partials in shared memory (fewer registers; used where
+// the larger layout fits), else in registers.
+template <int KMAX, bool GXS = false>
 __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
 {
     constexpr bool GP = KMAX > 0;
@@ -177,10 +183,11 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
     const int jb0 = w < W ? bstart(w) : n, jb1 = w < W ? bstart(w + 1) : n;  // this warp's block
     const int c = jb0 + lane;                                                  // this thread's column
     const bool own = c < jb1;
-    const PipeLayout lay = pipe_layout(n, k);
+    const PipeLayout lay = pipe_layout(n, k, GXS);
     float* Rs = reinterpret_cast<float*>(smem);
     float* ring = reinterpret_cast<float*>(smem + lay.ring);
     float* gbuf = reinterpret_cast<float*>(smem + lay.gbuf);
+    float* gxs = reinterpret_cast<float*>(smem + lay.gx);
     uint64_t* pub = reinterpret_cast<uint64_t*>(smem + lay.bars);  // [kD][kMaxW]
     uint64_t* fre = pub + kD * kMaxW;                               // [kD][kMaxW]
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + lay.flag);
@@ -210,29 +217,35 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
     const float* X = static_cast<const float*>(a.X);
 
     float av[kL];
-    float gacc[KMAX > 0 ? KMAX : 1];
+    float gacc[(!GXS && KMAX > 0) ? KMAX : 1];
 #pragma unroll
-    for (int q = 0; q < (KMAX > 0 ? KMAX : 1); ++q) gacc[q] = 0.f;
+    for (int q = 0; q < ((!GXS && KMAX > 0) ? KMAX : 1); ++q) gacc[q] = 0.f;
+    if (GXS && GP)
+        for (int e = (int)threadIdx.x; e < k * n; e += blockDim.x) gxs[e] = 0.f;
     float cs_acc = 0.f;
     bool bad = false;
 
-    // G' A(:, c) for this tile (original values of the column)
+    // G' A(:, c) for this tile (original values of the column), added to the
+    // column's binary32 partials; packed FMAs, .x over the even rows and .y over
+    // the odd ones
+    auto proj1 = [&](const float* gq) {
+        float2 p2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l4 = 0; l4 < kL / 4; ++l4) {
+            const float4 g = reinterpret_cast<const float4*>(gq)[l4];
+            p2 = __ffma2_rn(make_float2(g.x, g.y), make_float2(av[4 * l4], av[4 * l4 + 1]), p2);
+            p2 = __ffma2_rn(make_float2(g.z, g.w), make_float2(av[4 * l4 + 2], av[4 * l4 + 3]), p2);
+        }
+        return p2.x + p2.y;
+    };
     auto project = [&](const float* gs) {
+        if constexpr (GXS) {
+            if (!own) return;
+            for (int q = 0; q < k; ++q) gxs[q * n + c] += proj1(gs + q * kL);
+        } else {
 #pragma unroll
-        for (int q = 0; q < (KMAX > 0 ? KMAX : 1); ++q) {
-            if (q < k) {
-                const float4* gq = reinterpret_cast<const float4*>(gs + q * kL);
-                float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-                for (int l4 = 0; l4 < kL / 4; ++l4) {
-                    const float4 g = gq[l4];
-                    s0 = fmaf(g.x, av[4 * l4], s0);
-                    s1 = fmaf(g.y, av[4 * l4 + 1], s1);
-                    s0 = fmaf(g.z, av[4 * l4 + 2], s0);
-                    s1 = fmaf(g.w, av[4 * l4 + 3], s1);
-                }
-                gacc[q] += s0 + s1;
-            }
+            for (int q = 0; q < (KMAX > 0 ? KMAX : 1); ++q)
+                if (q < k) gacc[q] += proj1(gs + q * kL);
         }
     };
 
@@ -432,12 +445,19 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
             if (own && a.cs) a.cs[(size_t)cta * n + c] += (double)cs_acc;
             cs_acc = 0.f;
             if (GP && a.gx && own) {
-#pragma unroll
-                for (int q = 0; q < (KMAX > 0 ? KMAX : 1); ++q)
-                    if (q < k) {
-                        a.gx[((size_t)cta * k + q) * n + c] += (double)gacc[q];
-                        gacc[q] = 0.f;
+                if constexpr (GXS) {
+                    for (int q = 0; q < k; ++q) {
+                        a.gx[((size_t)cta * k + q) * n + c] += (double)gxs[q * n + c];
+                        gxs[q * n + c] = 0.f;
                     }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < (KMAX > 0 ? KMAX : 1); ++q)
+                        if (q < k) {
+                            a.gx[((size_t)cta * k + q) * n + c] += (double)gacc[q];
+                            gacc[q] = 0.f;
+                        }
+                }
             }
         }
     }
@@ -451,11 +471,14 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
     }
 }
 
-template <int KMAX>
+template <int KMAX, bool GXS>
 __global__ void __launch_bounds__(kMaxW * 32, 1) tsqr_pipe_kernel(const LeafArgs a)
 {
-    pipe_body<KMAX>(a, blockIdx.x);
+    pipe_body<KMAX, GXS>(a, blockIdx.x);
 }
+
+// The projection's partials go to shared memory where that layout fits.
+inline bool pipe_gxs(int n, int k) { return k > 0 && pipe_layout(n, k, true).total <= 220 * 1024; }
 
 // Batched form: CTA b runs stream desc[b].cta of problem desc[b].p (R from
 // zero, no projection); triangles and partial column sums go to the
@@ -483,11 +506,11 @@ __global__ void __launch_bounds__(kMaxW * 32, 1) tsqr_pipe_batched_kernel(const 
     pipe_body<0>(a, d.cta);
 }
 
-template <int KMAX>
-cudaError_t launch_pipe_k(const LeafArgs& a, int grid, cudaStream_t s)
+template <int KMAX, bool GXS>
+cudaError_t launch_pipe_kg(const LeafArgs& a, int grid, cudaStream_t s)
 {
-    const size_t smem = pipe_layout(a.n, KMAX > 0 ? a.k : 0).total;
-    auto kern = tsqr_pipe_kernel<KMAX>;
+    const size_t smem = pipe_layout(a.n, KMAX > 0 ? a.k : 0, GXS).total;
+    auto kern = tsqr_pipe_kernel<KMAX, GXS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (grid <= 0) return cudaSuccess;
@@ -497,16 +520,30 @@ cudaError_t launch_pipe_k(const LeafArgs& a, int grid, cudaStream_t s)
 }
 
 template <int KMAX>
-int pipe_ctas_per_sm_k(int n, int k)
+cudaError_t launch_pipe_k(const LeafArgs& a, int grid, cudaStream_t s)
 {
-    const size_t smem = pipe_layout(n, KMAX > 0 ? k : 0).total;
-    auto kern = tsqr_pipe_kernel<KMAX>;
+    if (KMAX > 0 && pipe_gxs(a.n, a.k)) return launch_pipe_kg<KMAX, KMAX != 0>(a, grid, s);
+    return launch_pipe_kg<KMAX, false>(a, grid, s);
+}
+
+template <int KMAX, bool GXS>
+int pipe_ctas_per_sm_kg(int n, int k)
+{
+    const size_t smem = pipe_layout(n, KMAX > 0 ? k : 0, GXS).total;
+    auto kern = tsqr_pipe_kernel<KMAX, GXS>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     int blocks = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, ((n + 31) / 32) * 32, smem) != cudaSuccess)
         return 1;
     return blocks < 1 ? 1 : blocks;
+}
+
+template <int KMAX>
+int pipe_ctas_per_sm_k(int n, int k)
+{
+    if (KMAX > 0 && pipe_gxs(n, k)) return pipe_ctas_per_sm_kg<KMAX, KMAX != 0>(n, k);
+    return pipe_ctas_per_sm_kg<KMAX, false>(n, k);
 }
 
 }  // namespace
