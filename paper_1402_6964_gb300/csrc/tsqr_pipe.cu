@@ -324,7 +324,7 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
                 float g1 = (ha + hb) + (hc + hd);
                 const float d0 = rv0[kL], rb0 = rv0[kL + 1], rd0 = rv0[kL + 2], c01 = rv0[kL + 3];
                 const float d1 = rv1[kL], rb1 = rv1[kL + 1], rd1 = rv1[kL + 2];
-                if (own) {
+                {  // a consumer (w >= 1) holds a full block: every lane owns its column
                     const int e0 = pk(j, n) + c, e1 = pk(j + 1, n) + c;
                     const float r0 = Rs[e0], r1 = Rs[e1];
                     const float wp0 = fmaf(d0, r0, g0);
@@ -358,7 +358,7 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
                 }
                 const float g = (ga + gb) + (gc + gd);
                 const float d = rv[kL], rb = rv[kL + 1], rd = rv[kL + 2];
-                if (own) {
+                {
                     const int e = pk(j, n) + c;
                     const float r = Rs[e];
                     const float wp = fmaf(d, r, g);
