@@ -25,6 +25,7 @@ struct LeafArgs {
     int* status;
     int tile_rows;         // warp leaf: tile height the pass was planned with (0 = warp_leaf_rows_per_tile)
     int tc_split;          // tensor-core leaf: 1 = three TF32 products (hi*hi + hi*lo + lo*hi), 0 = one
+    int ring_depth;        // pipelined leaf: tiles in flight in the reflector ring, 2 or 4 (0 = 2)
 };
 
 // Batched pass: one problem per entry, CTAs described one by one.

@@ -34,7 +34,7 @@ namespace mrnmf {
 namespace {
 
 constexpr int kL = 32;          // tile height
-constexpr int kD = 2;           // ring slots (tiles in flight)
+// ring slots (tiles in flight): 2, or 4 where the SM holds one CTA anyway (pipe_cfg)
 constexpr int kRS = kL + 4;     // ring entry: L values, then d, 1/beta, 1/d, v_j' v_(j+1)
 constexpr int kMaxW = 8;        // warps (n <= 256)
 constexpr int kFlushT = 32;     // tiles between binary64 flushes
@@ -48,7 +48,7 @@ struct PipeLayout {
 
 // gxs: the projection's binary32 partials in shared memory ([coordinate][column])
 // instead of registers
-__host__ __device__ inline PipeLayout pipe_layout(int n, int k, bool gxs = false)
+__host__ __device__ inline PipeLayout pipe_layout(int n, int k, bool gxs = false, int kD = 2)
 {
     const int kp = (k + 3) & ~3;
     PipeLayout p;
@@ -60,7 +60,7 @@ __host__ __device__ inline PipeLayout pipe_layout(int n, int k, bool gxs = false
     p.gx = off;
     if (gxs) off += up16(sizeof(float) * (size_t)k * n);
     p.bars = off;
-    off += sizeof(uint64_t) * 2 * kD * kMaxW;
+    off += sizeof(uint64_t) * 2 * kD * kMaxW;  // pub[kD][kMaxW], fre[kD][kMaxW]
     p.flag = off;
     off += 16;
     p.total = off;
@@ -183,7 +183,9 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
     const int jb0 = w < W ? bstart(w) : n, jb1 = w < W ? bstart(w + 1) : n;  // this warp's block
     const int c = jb0 + lane;                                                  // this thread's column
     const bool own = c < jb1;
-    const PipeLayout lay = pipe_layout(n, k, GXS);
+    const int kD = a.ring_depth == 4 ? 4 : 2;  // tiles in flight
+    const int lgD = kD == 4 ? 2 : 1;
+    const PipeLayout lay = pipe_layout(n, k, GXS, kD);
     float* Rs = reinterpret_cast<float*>(smem);
     float* ring = reinterpret_cast<float*>(smem + lay.ring);
     float* gbuf = reinterpret_cast<float*>(smem + lay.gbuf);
@@ -252,7 +254,7 @@ __device__ __forceinline__ void pipe_body(const LeafArgs& a, const int cta)
     int64_t t = 0;
     for (; t < ntiles; ++t) {
         const int s = (int)(t & (kD - 1));
-        const uint32_t par = (uint32_t)((t / kD) & 1);
+        const uint32_t par = (uint32_t)((t >> lgD) & 1);
         const uint32_t par_prev = par ^ 1u;  // the slot's previous use (tile t - kD)
         const int64_t row0 = r0 + t * kL;
         const int rows_v = (int)min((int64_t)kL, r1 - row0);
@@ -477,8 +479,28 @@ __global__ void __launch_bounds__(kMaxW * 32, 1) tsqr_pipe_kernel(const LeafArgs
     pipe_body<KMAX, GXS>(a, blockIdx.x);
 }
 
-// The projection's partials go to shared memory where that layout fits.
-inline bool pipe_gxs(int n, int k) { return k > 0 && pipe_layout(n, k, true).total <= 220 * 1024; }
+// Ring depth and the projection partials' place for n columns and k projection
+// rows.  Four tiles in flight where the two-slot layout already leaves one CTA
+// per SM (more than half of the SM's shared memory) and four fit: the
+// wavefront of a tile through the warps then has room; measured on GB300 at
+// n = 200: 106.7 -> 118.3 GB/s (k = 0), 181.7 -> 157.8 ms per 2e7 rows
+// (k = 40).  Where several CTAs fit, two slots keep them (n = 100: 286 GB/s
+// with two, 184 with four).  The projection's partials go to shared memory
+// where that layout still fits, else to registers.
+struct PipeCfg {
+    int depth;
+    bool gxs;
+};
+
+inline PipeCfg pipe_cfg(int n, int k)
+{
+    constexpr size_t cap = 220 * 1024;
+    if (pipe_layout(n, k, false, 2).total > 113 * 1024) {
+        if (k > 0 && pipe_layout(n, k, true, 4).total <= cap) return {4, true};
+        if (pipe_layout(n, k, false, 4).total <= cap) return {4, false};
+    }
+    return {2, k > 0 && pipe_layout(n, k, true, 2).total <= cap};
+}
 
 // Batched form: CTA b runs stream desc[b].cta of problem desc[b].p (R from
 // zero, no projection); triangles and partial column sums go to the
@@ -509,7 +531,7 @@ __global__ void __launch_bounds__(kMaxW * 32, 1) tsqr_pipe_batched_kernel(const 
 template <int KMAX, bool GXS>
 cudaError_t launch_pipe_kg(const LeafArgs& a, int grid, cudaStream_t s)
 {
-    const size_t smem = pipe_layout(a.n, KMAX > 0 ? a.k : 0, GXS).total;
+    const size_t smem = pipe_layout(a.n, KMAX > 0 ? a.k : 0, GXS, a.ring_depth == 4 ? 4 : 2).total;
     auto kern = tsqr_pipe_kernel<KMAX, GXS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -520,16 +542,19 @@ cudaError_t launch_pipe_kg(const LeafArgs& a, int grid, cudaStream_t s)
 }
 
 template <int KMAX>
-cudaError_t launch_pipe_k(const LeafArgs& a, int grid, cudaStream_t s)
+cudaError_t launch_pipe_k(const LeafArgs& a0, int grid, cudaStream_t s)
 {
-    if (KMAX > 0 && pipe_gxs(a.n, a.k)) return launch_pipe_kg<KMAX, KMAX != 0>(a, grid, s);
+    const PipeCfg cfg = pipe_cfg(a0.n, KMAX > 0 ? a0.k : 0);
+    LeafArgs a = a0;
+    a.ring_depth = cfg.depth;
+    if (KMAX > 0 && cfg.gxs) return launch_pipe_kg<KMAX, KMAX != 0>(a, grid, s);
     return launch_pipe_kg<KMAX, false>(a, grid, s);
 }
 
 template <int KMAX, bool GXS>
-int pipe_ctas_per_sm_kg(int n, int k)
+int pipe_ctas_per_sm_kg(int n, int k, int depth)
 {
-    const size_t smem = pipe_layout(n, KMAX > 0 ? k : 0, GXS).total;
+    const size_t smem = pipe_layout(n, KMAX > 0 ? k : 0, GXS, depth).total;
     auto kern = tsqr_pipe_kernel<KMAX, GXS>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
@@ -542,8 +567,9 @@ int pipe_ctas_per_sm_kg(int n, int k)
 template <int KMAX>
 int pipe_ctas_per_sm_k(int n, int k)
 {
-    if (KMAX > 0 && pipe_gxs(n, k)) return pipe_ctas_per_sm_kg<KMAX, KMAX != 0>(n, k);
-    return pipe_ctas_per_sm_kg<KMAX, false>(n, k);
+    const PipeCfg cfg = pipe_cfg(n, KMAX > 0 ? k : 0);
+    if (KMAX > 0 && cfg.gxs) return pipe_ctas_per_sm_kg<KMAX, KMAX != 0>(n, k, cfg.depth);
+    return pipe_ctas_per_sm_kg<KMAX, false>(n, k, cfg.depth);
 }
 
 }  // namespace
