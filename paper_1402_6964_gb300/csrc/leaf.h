@@ -61,7 +61,7 @@ cudaError_t launch_warp_batched(const BatchCta* desc, int nctas, const BatchProb
                                 int* status, cudaStream_t s);
 int warp_batched_rows_per_tile(int family);
 
-// Lane-group leaf (tsqr_group.cu): binary32, n <= 16, no projection; four
+// Lane-group leaf (tsqr_group.cu): binary32, n <= 28, no projection; four
 // warps per CTA, one stream of the pass per warp (32/S Householder streams of
 // S lanes inside it, folded at the end of the launch).  The warp leaf's
 // functions dispatch to it; MRNMF_GROUP_LEAF=0 turns it off.

@@ -1,13 +1,14 @@
-"""The lane-group leaf (n <= 16, no projection) against the FP64 oracle.
+"""The lane-group leaf (n <= 28, no projection) against the FP64 oracle.
 
-Every binary32 pass with n <= 16 and k = 0 runs on it: a warp holds 32/S
-Householder streams of S = 4, 8 or 16 lanes, each on an interleaved share of
+Every binary32 pass with n <= 28 and k = 0 runs on it: a warp holds 32/S
+Householder streams of S = 4, 8, 16 or 32 lanes, each on an interleaved share of
 the warp's super-tiles, folded into one triangle per CTA at the end of the
 launch.  Checked here, element by element against the oracle (R within the
 FP32 pass tolerance, relative Frobenius 1e-5; column sums within relative
 1e-6):
 
-* every n from 1 to 16, so each group size and each partly filled group;
+* every n from 1 to 16 and six widths from 17 to 28, so each group size and
+  each partly filled group;
 * row counts below one super-tile, at ragged multiples, and large enough for
   many tiles per stream and several binary64 flushes of the column sums;
 * strided rows (ldx > n) and a base address off the 16-byte grid, which take
@@ -57,7 +58,7 @@ def check(oracle, X, R, cs):
     np.testing.assert_allclose(host(cs), oracle.colsum(X64), rtol=CS_RTOL)
 
 
-@pytest.mark.parametrize("n", list(range(1, 17)))
+@pytest.mark.parametrize("n", list(range(1, 17)) + [17, 18, 20, 24, 25, 28])
 def test_every_width_matches_oracle(h, oracle, n):
     from paper_1402_6964_gb300 import mrnmf
     assert mrnmf.tune_leaf_rows(n, 0) in (64, 128, 256, 512)  # the group leaf's super-tile
@@ -68,7 +69,7 @@ def test_every_width_matches_oracle(h, oracle, n):
         check(oracle, X, R, cs)
 
 
-@pytest.mark.parametrize("m,n", [(2_000_003, 8), (1_500_001, 13), (3_000_000, 4)])
+@pytest.mark.parametrize("m,n", [(2_000_003, 8), (1_500_001, 13), (3_000_000, 4), (1_000_003, 25), (800_001, 28)])
 def test_many_tiles_per_stream(h, oracle, m, n):
     # tens of super-tiles per stream: several binary64 flushes of the column sums
     X = synth.random_nonneg(m, n, seed=m % 1000 + n)
@@ -77,7 +78,7 @@ def test_many_tiles_per_stream(h, oracle, m, n):
     check(oracle, X, R, cs)
 
 
-@pytest.mark.parametrize("n", [3, 8, 12, 16])
+@pytest.mark.parametrize("n", [3, 8, 12, 16, 25, 28])
 def test_direct_load_paths(h, oracle, n):
     W = synth.random_nonneg(50_001, n + 5, seed=n)
     Xs = torch.from_numpy(W).cuda()[:, 2:2 + n]            # ldx = n + 5
@@ -92,7 +93,7 @@ def test_direct_load_paths(h, oracle, n):
     check(oracle, host(Xo), R, cs)
 
 
-@pytest.mark.parametrize("n", [5, 8, 16])
+@pytest.mark.parametrize("n", [5, 8, 16, 25])
 def test_stream_in_ragged_chunks(h, oracle, n):
     X = synth.random_nonneg(700_007, n, seed=400 + n)
     Xd = torch.from_numpy(X).cuda()
@@ -126,7 +127,7 @@ def test_input_check(h, oracle):
     h.sync()
 
 
-@pytest.mark.parametrize("n", [6, 12, 16])
+@pytest.mark.parametrize("n", [6, 12, 16, 24, 28])
 def test_ill_conditioned_columns(h, oracle, n):
     X, _ = synth.planted_separable(400_000, n, max(2, n // 3), seed=1404000 + n, noise=1e-3, decades=6.0)
     R, cs = h.tsqr_r(torch.from_numpy(X).cuda(), prec="fp32")

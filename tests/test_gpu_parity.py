@@ -536,7 +536,7 @@ def test_tuned_stream_counts_match_oracle(h, oracle, tmp_path):
         mrnmf.tune_load(None)
 
 
-@pytest.mark.parametrize("n,k,rows", [(20, 0, 128), (20, 12, 128), (50, 0, 64), (50, 20, 64), (60, 20, 64),
+@pytest.mark.parametrize("n,k,rows", [(30, 0, 128), (20, 12, 128), (50, 0, 64), (50, 20, 64), (60, 20, 64),
                                       (64, 0, 64)])
 def test_tuned_tile_heights_match_oracle(h, oracle, tmp_path, n, k, rows):
     """A rows line changes the warp leaf's tile height; R, the column sums and

@@ -51,22 +51,23 @@ def test_missing_file_and_clear(mrnmf, tmp_path):
 
 
 def test_rows_lines_pick_the_warp_leaf_tile_height(mrnmf, tmp_path):
-    # built-in heights: 64 rows for n <= 32 (one column per lane), 32 for 33..64
-    assert [mrnmf.tune_leaf_rows(n, k) for n, k in [(20, 0), (20, 12), (50, 0), (50, 20)]] == [64, 64, 32, 32]
+    # built-in heights: 64 rows for n <= 32 (one column per lane; with the
+    # projection, since the lane-group leaf serves k = 0 there), 32 for 33..64
+    assert [mrnmf.tune_leaf_rows(n, k) for n, k in [(20, 12), (50, 0), (50, 20)]] == [64, 32, 32]
     assert mrnmf.tune_leaf_rows(100, 0) == 0   # not the warp leaf's
-    path = _write(tmp_path, "rows 33 64 0 0 64\nrows 1 32 0 64 128\nrows 1 64 0 64 32\n")
+    path = _write(tmp_path, "rows 33 64 0 0 64\nrows 1 32 1 64 128\nrows 1 64 0 64 32\n")
     assert mrnmf.tune_load(path) == mrnmf.OK
     assert mrnmf.tune_leaf_rows(50, 0) == 64   # first matching line
     assert mrnmf.tune_leaf_rows(50, 20) == 32  # k = 20 outside [0, 0]: third line
-    assert mrnmf.tune_leaf_rows(20, 0) == 128
     assert mrnmf.tune_leaf_rows(20, 12) == 128
+    assert mrnmf.tune_leaf_rows(20, 0) == 64   # the lane-group leaf's super-tile, whatever the table says
     assert mrnmf.tune_leaf_rows(100, 0) == 0
 
 
 def test_rows_line_the_form_cannot_take_gives_the_default(mrnmf, tmp_path):
     # 32 rows is not a height of the one-column form, 128 not one of the two-column form
     assert mrnmf.tune_load(_write(tmp_path, "rows 1 32 0 64 32\nrows 33 64 0 64 128\n")) == mrnmf.OK
-    assert mrnmf.tune_leaf_rows(20, 0) == 64
+    assert mrnmf.tune_leaf_rows(20, 12) == 64
     assert mrnmf.tune_leaf_rows(50, 0) == 32
     # n = 64 with 64 projection rows: four 64-row slices need 232 KB of shared memory
     assert mrnmf.tune_load(_write(tmp_path, "rows 33 64 0 64 64\n")) == mrnmf.OK
@@ -94,10 +95,12 @@ def test_leaf_rows_query_rejects_bad_arguments(mrnmf):
 
 
 def test_lane_group_leaf_heights_are_fixed(mrnmf, tmp_path):
-    # n <= 16 without the projection runs on the lane-group leaf: super-tiles of
-    # 32 * 64/S rows (S = 4, 8, 16 lanes a stream), which rows lines do not change;
-    # with the projection the warp leaf serves those widths and follows the table
-    assert mrnmf.tune_load(_write(tmp_path, "rows 1 16 0 64 128\n")) == mrnmf.OK
-    assert [mrnmf.tune_leaf_rows(n, 0) for n in (1, 4, 5, 8, 9, 16)] == [512, 512, 256, 256, 128, 128]
+    # n <= 28 without the projection runs on the lane-group leaf: super-tiles of
+    # 32 * 64/S rows (S = 4, 8, 16, 32 lanes a stream), which rows lines do not
+    # change; with the projection the warp leaf serves those widths and follows the table
+    assert mrnmf.tune_load(_write(tmp_path, "rows 1 32 0 64 128\n")) == mrnmf.OK
+    assert [mrnmf.tune_leaf_rows(n, 0) for n in (1, 4, 5, 8, 9, 16, 17, 28)] == [512, 512, 256, 256, 128, 128, 64, 64]
     assert mrnmf.tune_leaf_rows(8, 12) == 128
-    assert mrnmf.tune_leaf_rows(17, 0) == 64
+    assert mrnmf.tune_leaf_rows(25, 16) == 128
+    assert mrnmf.tune_leaf_rows(32, 0) == 128   # n = 29..32 without the projection: the warp leaf again
+    assert mrnmf.tune_leaf_rows(33, 0) == 32
