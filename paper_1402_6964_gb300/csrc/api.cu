@@ -96,7 +96,9 @@ mrnmf_status check_pass_args(mrnmf_handle* h, const void* X, int64_t m, int32_t 
 }
 
 // Set up h->st for a pass: precision, stream count, workspace.
-mrnmf_status setup_pass(mrnmf_handle* h, int n, int dtype, int prec, int k, uint64_t seed, int64_t m_hint)
+// qr = 0 is a projection-only pass; gp_form names its tensor-core form (0: SIMT).
+mrnmf_status setup_pass(mrnmf_handle* h, int n, int dtype, int prec, int k, uint64_t seed, int64_t m_hint, int qr = 1,
+                        int gp_form = 0)
 {
     prec = resolve_prec(prec, dtype, n, k);
     if (prec == MRNMF_PREC_FP32 && dtype == MRNMF_F64)
@@ -111,7 +113,9 @@ mrnmf_status setup_pass(mrnmf_handle* h, int n, int dtype, int prec, int k, uint
     st.tree64 = !st.fp64 && mrnmf::tree64_requested() && mrnmf::tree64_supported(n);
     st.seed = seed;
     st.rows_seen = 0;
-    st.P = mrnmf::choose_streams(n, k, st.fp64, st.tc, m_hint);
+    const bool gp_warp = !qr && !st.fp64 && dtype == MRNMF_F32 && k > 0 && mrnmf::gp_pass_form(gp_form) == 0 &&
+                         mrnmf::gp_warp_supported(n, k);
+    st.P = gp_warp ? mrnmf::gp_warp_streams(n, k, m_hint) : mrnmf::choose_streams(n, k, st.fp64, st.tc, m_hint);
     mrnmf_status s = grow(h, &h->ws, &h->ws_bytes, mrnmf::pass_state_bytes(n, k, st.P, st.fp64), "pass workspace");
     if (s != MRNMF_OK) return s;
     mrnmf::pass_state_carve(st, h->ws);
@@ -125,7 +129,7 @@ mrnmf_status run_pass(mrnmf_handle* h, const void* X, int64_t m, int32_t n, int6
                       int qr, double* R, double* colsum, int32_t k, uint64_t seed, int64_t row_offset, double* GX,
                       cudaStream_t s, int gp_form)
 {
-    mrnmf_status st = setup_pass(h, n, dtype, prec, k, seed, m);
+    mrnmf_status st = setup_pass(h, n, dtype, prec, k, seed, m, qr, gp_form);
     if (st != MRNMF_OK) return st;
     h->st.rows_seen = row_offset;
     h->st.gp_form = gp_form;

@@ -57,6 +57,10 @@ int tune_leaf_rows(int n, int k);  // the table's warp-leaf tile height for (n, 
 // Number of streams for a pass over about `m` rows (0 = unknown / streaming).
 int choose_streams(int n, int k, int fp64, int tc, int64_t m);
 
+// The tensor-core form a projection-only pass takes: gp_form if nonzero, else
+// MRNMF_PREC_TF32X3 under MRNMF_GP_TC=1, else 0 (the SIMT pass).
+int gp_pass_form(int gp_form);
+
 // Zero the state (triangles and partials) for a new pass.
 cudaError_t pass_reset(const PassState& st, cudaStream_t s);
 

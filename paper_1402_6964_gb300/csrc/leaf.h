@@ -87,6 +87,14 @@ cudaError_t launch_pipe_leaf(const LeafArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_pipe_batched(const BatchCta* desc, int nctas, const BatchProblem* probs, int max_n, int* status,
                                 cudaStream_t s);
 
+// Projection-only pass (gp_simt.cu): binary32, n <= 64, 1 <= k <= 32, no
+// triangle; one stream per warp, four per CTA.  MRNMF_GP_WARP=0 turns it off.
+bool gp_warp_supported(int n, int k);
+int gp_warp_rows_per_tile();
+int gp_warp_streams_per_cta();
+int gp_warp_streams(int n, int k, int64_t m);  // streams that fill the GPU for about m rows (0 = unknown)
+cudaError_t launch_gp_warp(const LeafArgs& a, int streams, cudaStream_t s);
+
 // Tensor-core leaf (tsqr_wy.cu): 16 < n <= 128; one stream per CTA.
 int tc_leaf_rows_per_tile();
 int tc_leaf_ctas_per_sm(int n);

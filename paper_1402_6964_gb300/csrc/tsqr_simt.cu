@@ -446,6 +446,19 @@ static int choose_streams_default(int n, int k, int fp64, int tc, int64_t m)
     return std::max(P, 1);
 }
 
+// The projection-only pass runs on the SIMT cores by default: G's generation
+// (Philox + Box-Muller), not the k-by-n product, dominates it, and the tcgen05
+// forms measured slower on GB300.  MRNMF_GP_TC=1 selects the tcgen05 (3-pass
+// TF32) form; mrnmf_gauss_project_tc names a tcgen05 form explicitly.
+int gp_pass_form(int gp_form)
+{
+    static const bool gp_tc = [] {
+        const char* v = getenv("MRNMF_GP_TC");
+        return v && v[0] == '1';
+    }();
+    return gp_form ? gp_form : (gp_tc ? MRNMF_PREC_TF32X3 : 0);
+}
+
 cudaError_t pass_reset(const PassState& st, cudaStream_t s)
 {
     const size_t ts = st.fp64 ? 8 : 4;
@@ -484,20 +497,18 @@ cudaError_t pass_push(PassState& st, const void* X, int64_t rows, int64_t ldx, i
     const bool warp_path = !st.fp64 && !xf64 && qr && warp_leaf_supported(st.n, st.k) &&
                            st.P % warp_leaf_warps_per_cta() == 0;
     st.tri = st.P;
-    // The projection-only pass runs on SIMT cores by default: G's generation
-    // (Philox + Box-Muller), not the k-by-n product, dominates it, and the
-    // tcgen05 form measured slower on GB300 (525 vs 727 GB/s at 1e7 x 50, k = 20).
-    // MRNMF_GP_TC=1 selects the tcgen05 (3-pass TF32) form; mrnmf_gauss_project_tc
-    // names a tcgen05 form explicitly (st.gp_form).
-    static const bool gp_tc = [] {
-        const char* v = getenv("MRNMF_GP_TC");
-        return v && v[0] == '1';
-    }();
-    const int gp_form = st.gp_form ? st.gp_form : (gp_tc ? MRNMF_PREC_TF32X3 : 0);
+    const int gp_form = gp_pass_form(st.gp_form);
     if (!qr && !st.fp64 && !xf64 && st.k > 0 && gp_form && gp_tc_supported(st.n, st.k)) {
         // projection-only pass on the tensor cores
         e = launch_gp_tc(static_cast<const float*>(X), rows, ldx, st.n, st.k, st.rows_seen, st.seed, st.P, st.cs,
                          st.gx, status, gp_form == MRNMF_PREC_BF16, s);
+    } else if (!qr && !st.fp64 && !xf64 && st.k > 0 && gp_warp_supported(st.n, st.k) &&
+               st.P % gp_warp_streams_per_cta() == 0) {
+        // projection-only pass, one warp per stream
+        const int L = gp_warp_rows_per_tile();
+        int64_t pw = (rows + st.P - 1) / st.P;
+        a.rows_per_cta = ((pw + L - 1) / L) * L;
+        e = launch_gp_warp(a, st.P, s);
     } else if (st.tc && !xf64 && qr) {
         a.tc_split = st.tc == 1;
         const int L = tc_leaf_rows_per_tile();
