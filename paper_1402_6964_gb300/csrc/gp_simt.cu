@@ -9,7 +9,7 @@
 //   - lane l draws row l of G (k Gaussians: Philox4x32-10 and Box-Muller,
 //     keyed by the global row, the same generator as the fused leaves) into a
 //     coordinate-major buffer, G(q, 0..31) contiguous;
-//   - lane l holds columns l and l + 32 of the tile in registers;
+//   - lane l holds column l of the tile (and l + 32 when n > 32) in registers;
 //   - for each coordinate q, lane l forms G(q,:) . X(:, c) for its columns with
 //     packed FMAs (even and odd rows in the two halves of a float2, rows 0-15
 //     and 16-31 in separate chains), reading G(q,:) as broadcast 16-byte loads,
