@@ -34,9 +34,9 @@ template <int S>
 __host__ __device__ constexpr int part_group() { return S * part_col<S>() + 16; }  // floats per group
 
 // Per-warp shared memory: [mbarrier | super-tile (32 * 64/S) x n | fold pivots
-// 2 x (32/S) x (fold_rows + 4) | partial dots (32/S) x part_group (n > 8)].  After the tile
-// loop the super-tile area holds the groups' triangles for the fold
-// ((32/S) n^2 <= 32 (64/S) n floats).
+// 2 x (32/S) x (fold_rows + 4) | partial dots (32/S) x part_group, then update factors
+// (32/S) x 32 (n > 8)].  After the tile loop the super-tile area holds the groups'
+// triangles for the fold ((32/S) n^2 <= 32 (64/S) n floats).
 template <int NC>
 __host__ __device__ constexpr bool group_smem_sums() { return group_lanes(NC) >= 16; }
 
@@ -47,7 +47,7 @@ template <int NC>
 __host__ __device__ inline size_t group_slice_bytes()
 {
     constexpr int S = group_lanes(NC), TR = 32 * (64 / S);
-    const size_t red = group_smem_sums<NC>() ? sizeof(float) * (32 / S) * part_group<S>() : 0;
+    const size_t red = group_smem_sums<NC>() ? sizeof(float) * (32 / S) * (part_group<S>() + 32) : 0;
     return gup(128 + gup(sizeof(float) * (size_t)TR * NC, 128) + sizeof(float) * group_pub_floats<NC>() + red, 128);
 }
 
@@ -172,12 +172,37 @@ __device__ __forceinline__ void row_step(float2 (&A2)[64 / group_lanes(NC) / 2][
             r[J] = hs.beta;
         }
     }
+    if constexpr (group_smem_sums<NC>()) {
+        // 16- and 32-lane groups: lane c publishes its factor, and every lane
+        // reads the live ones as broadcast 16-byte loads (one load per four
+        // columns instead of a shuffle per column).  The next step's factors
+        // are written only after its partial sums, which every lane reaches
+        // after these reads.
+        float* fb = red + (32 / S) * part_group<S>() + g * 32;
+        if (own && s > J) fb[s] = fs;
+        __syncwarp();
 #pragma unroll
-    for (int c = J + 1; c < NC; ++c) {
-        const float fc = __shfl_sync(FULL, fs, lead + c);
-        const float2 f2 = make_float2(fc, fc);
+        for (int c4 = (J + 1) & ~3; c4 < NC; c4 += 4) {
+            const float4 f = *reinterpret_cast<const float4*>(fb + c4);
+            const float fv[4] = {f.x, f.y, f.z, f.w};
 #pragma unroll
-        for (int p = 0; p < RP; ++p) A2[p][c] = __ffma2_rn(f2, A2[p][J], A2[p][c]);
+            for (int u = 0; u < 4; ++u) {
+                const int c = c4 + u;
+                if (c > J && c < NC) {
+                    const float2 f2 = make_float2(fv[u], fv[u]);
+#pragma unroll
+                    for (int p = 0; p < RP; ++p) A2[p][c] = __ffma2_rn(f2, A2[p][J], A2[p][c]);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = J + 1; c < NC; ++c) {
+            const float fc = __shfl_sync(FULL, fs, lead + c);
+            const float2 f2 = make_float2(fc, fc);
+#pragma unroll
+            for (int p = 0; p < RP; ++p) A2[p][c] = __ffma2_rn(f2, A2[p][J], A2[p][c]);
+        }
     }
 }
 
