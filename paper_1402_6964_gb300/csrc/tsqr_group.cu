@@ -13,11 +13,15 @@
 // lane holds whole rows: 64/S rows of the group's 64-row block, all n columns,
 // in registers.  The pivot column of a step is then local to each lane; what
 // crosses lanes is the vector of dot products g_c = A(:, j) . A(:, c) of the
-// live columns c >= j (summed over the group's lanes by xor shuffles) and one
-// scalar per column for the update.  Lane s of a group also holds column s of
-// the group's triangle (r[i] = R(i, s), i <= s).  n is a template parameter,
-// so the finished columns c < j cost nothing, and the dot products and the
-// update run on packed binary32 FMAs (two rows per instruction).
+// live columns c >= j and one scalar per column for the update.  Groups of 4
+// and 8 lanes sum the dot products by xor shuffles and broadcast the scalars
+// by shuffles; groups of 16 and 32 lanes pass both through shared memory
+// (each lane's partials stored transposed and summed by the lane that owns
+// the column, the scalars read back four at a time).  Lane s of a group also
+// holds column s of the group's triangle (r[i] = R(i, s), i <= s).  n is a
+// template parameter, so the finished columns c < j cost nothing, and the dot
+// products and the update run on packed binary32 FMAs (two rows per
+// instruction).
 //
 // The pass sees one stream per warp, as with the warp leaf: the warp stages
 // super-tiles of 32 * 64/S consecutive rows by one bulk copy, lane l taking
