@@ -169,7 +169,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_gp_pass(args):
+def run_gp_pass(args, quiet=False):
     """Projection-only pass: GB/s of X, SIMT (mrnmf_gauss_project) or a tensor-core
     form (mrnmf_gauss_project_tc, --gp-form tf32x3 | bf16)."""
     import torch
@@ -199,14 +199,19 @@ def run_gp_pass(args):
     ms = a.elapsed_time(b) / args.steps
     hbm, _, src = _peaks()
     gbs = 4.0 * X.shape[0] * X.shape[1] / ms / 1e6
-    print(json.dumps({"mode": "gp", "metric": "Gaussian projection pass GB/s of X", "value": gbs, "unit": "GB/s",
-                      "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
-                      "path": ("tcgen05 " + args.gp_form) if args.gp_form != "simt"
-                      else ("tcgen05 tf32x3" if os.environ.get("MRNMF_GP_TC") == "1" else "simt"),
-                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                                   "frac": gbs / hbm, "peak_source": src},
-                      "config": {"workload": w.name, "m": X.shape[0], "n": w.n, "k": w.k}}), flush=True)
+    line = {"mode": "gp", "metric": "Gaussian projection pass GB/s of X", "value": gbs, "unit": "GB/s",
+            "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+            "path": ("tcgen05 " + args.gp_form) if args.gp_form != "simt"
+            else ("tcgen05 tf32x3" if os.environ.get("MRNMF_GP_TC") == "1" else "simt"),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": gbs / hbm, "peak_source": src},
+            "config": {"workload": w.name, "m": X.shape[0], "n": w.n, "k": w.k}}
     h.close()
+    del Xd
+    torch.cuda.empty_cache()
+    if not quiet:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_pass(args):
@@ -907,6 +912,15 @@ def run_ours(args):
             other["per_n_fp32_pass"] = per_n_sweep(sms, mhz, hbm)
         except Exception as ex:
             other["per_n_fp32_pass"] = {"error": str(ex)[:300]}
+        # the projection-only pass (GP alone) on the benchmarked workload, in the
+        # default SIMT form and the tcgen05 BF16 form
+        for form in ("simt", "bf16"):
+            try:
+                sub = argparse.Namespace(**vars(args))
+                sub.rows, sub.steps, sub.warmup, sub.gp_form = None, 10, 3, form
+                other[f"gp_projection_{form}"] = run_gp_pass(sub, quiet=True)
+            except Exception as ex:
+                other[f"gp_projection_{form}"] = {"error": str(ex)[:300]}
         for name, fn in (("illcond_1e8x200_forms", run_illcond_forms), ("fc_stream_1p6e9x25", run_stream),
                          ("batch_256", run_batched)):
             try:
